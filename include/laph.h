@@ -1,0 +1,277 @@
+/*
+ * laph.h -- C ABI of the GB300 (sm_103a) stochastic-LapH quark-line library.
+ *
+ * The library computes, on one GPU, the four steps of the stochastic LapH
+ * method of Morningstar et al., "Improved stochastic estimation of quark
+ * propagation with Laplacian Heaviside smearing in lattice QCD"
+ * (arXiv:1104.3870):
+ *   (a) the lowest N_v eigenpairs of the 3D gauge-covariant Laplacian on every
+ *       time slice (Sec. II, Laplacian and LapH smearing; Sec. IV, KSRL with
+ *       Chebyshev acceleration)                                   laph_eigvecs
+ *   (b) Z4 noise in the LapH subspace, diluted sources
+ *       varrho = V_s P^(b) rho (Sec. II, Eq. (varrhodef); Sec. IV noise)
+ *                                                            laph_make_sources
+ *   (c) solves of Omega x = y, Omega = gamma_4 K, for every diluted source
+ *       (Sec. II quark line; Sec. IV solver)               dirac_solve_batch
+ *   (d) sink coefficients V_s^dag x (Sec. IV) and meson / two-pion
+ *       correlators (Sec. III, Eqs. (mesonfunc), (mesoncorr))  laph_sinks,
+ *                                                                 correlate
+ * plus the gauge preparation (stout smearing, Sec. II) in laph_stout_smear.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Every array argument is a plain pointer to caller-owned memory, either
+ *    device memory of the context's GPU or host memory (pageable or pinned);
+ *    the library detects which with cudaPointerGetAttributes and stages host
+ *    arrays through its own device workspace.  The library never frees or
+ *    retains caller memory past the call.
+ *  * Complex numbers are interleaved (re, im) doubles ("c128").
+ *  * Sites are ordered lexicographically with x fastest:
+ *      site = ((t * ns + z) * ns + y) * ns + x,  V3 = ns^3, V = V3 * nt.
+ *    Gauge links:   [V][mu = x,y,z,t][3][3]  c128 (row index first).
+ *    Spinor fields: [V][spin 4][colour 3]    c128.
+ *    Eigenvectors:  [nt][nv][V3][colour 3]   c128 (orthonormal per slice).
+ *    Z4 noise:      uint8 code v[nt][spin 4][nv], rho = i^v.
+ *    Coefficients:  [nrhs][nt][spin 4][nv]   c128.
+ *  * Dirac matrices are in the chiral basis (gamma_5 = diag(1,1,-1,-1)).
+ *  * ns and nt must be even (even-odd ordering); ns >= 2, nt >= 2.
+ *  * Calls are issued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream).  A call returns after its work is queued unless it writes host
+ *    memory or a report, in which case it synchronises `stream` first.
+ *  * Return value: LAPH_OK or an error code; laph_last_error() then gives a
+ *    message (thread-local).  No C++ exception crosses the ABI.
+ */
+#ifndef LAPH_H
+#define LAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LAPH_OK = 0,
+    LAPH_ERR_ARG = 1,            /* invalid argument (sizes, dilution, pointers)      */
+    LAPH_ERR_CUDA = 2,           /* a CUDA runtime call failed                         */
+    LAPH_ERR_NOT_CONVERGED = 3,  /* outputs written but above tolerance (see report)   */
+    LAPH_ERR_TIMEOUT = 4,        /* a bounded device wait gave up                      */
+    LAPH_ERR_NOMEM = 5           /* workspace allocation failed                        */
+};
+
+typedef struct laph_ctx laph_ctx;
+
+typedef struct {
+    int ns;        /* spatial extent L (lattice L^3 x nt), even */
+    int nt;        /* temporal extent, even                      */
+    double xi;     /* anisotropy a_s / a_t                        */
+} laph_lattice;
+
+/* Creates a context on CUDA device `device` (workspace, autotune cache). */
+int laph_ctx_create(int device, laph_ctx **out);
+void laph_ctx_destroy(laph_ctx *ctx);
+/* Message of the last error on this thread ("" if none). */
+const char *laph_last_error(void);
+/* Library version string. */
+const char *laph_version(void);
+
+/* ------------------------------------------------------------------------
+ * Gauge preparation: stout smearing (Sec. II: spatial links smeared with
+ * the stout recipe, only spatial staples, temporal links not smeared).
+ *   links        [V][4][3][3] c128, smeared in place.
+ *   rho          staple weight (0.1 in the paper).
+ *   nsteps       number of stout steps.
+ *   spatial_only 1: staples and updates over spatial directions only (the
+ *                paper's 3D smearing); 0: all four directions (4D).
+ * Each step computes C_mu = rho sum_{nu != mu} staples, Omega = C_mu U_mu^dag,
+ * Q = (i/2)(Omega^dag - Omega) - (i/6) Tr(Omega^dag - Omega),
+ * U_mu <- exp(iQ) U_mu for all links at once.  Errors: LAPH_ERR_ARG for bad
+ * sizes or a null pointer.
+ * ------------------------------------------------------------------------ */
+int laph_stout_smear(laph_ctx *ctx, const laph_lattice *lat, void *links, double rho,
+                     int nsteps, int spatial_only, void *stream);
+
+/* ------------------------------------------------------------------------
+ * (a) Laplacian eigenvectors (Sec. II: V_s holds the eigenvectors of the N_v
+ * lowest eigenvalues of -Delta on each time slice; Sec. IV: Krylov-spectral
+ * restarted Lanczos with Chebyshev acceleration A = T_n(B),
+ * B = 1 + 2 (Delta + lambda_C)/(lambda_L - lambda_C), full
+ * reorthogonalisation repeated while the norm drops by 1/sqrt(2), at most 4).
+ *   links3d  [V][4][3][3] c128: stout-smeared links (slots x,y,z used).
+ *   nv       number of eigenpairs per slice, 1 <= nv <= 3 V3 / 2.
+ *   evals    [nt][nv] doubles, ascending eigenvalues of -Delta.
+ *   evecs    [nt][nv][V3][3] c128; each vector has the phase convention
+ *            applied: its largest-modulus component (the first in storage
+ *            order among those within a relative 1e-8 of the largest) is real
+ *            and positive.
+ *   params   NULL for defaults (lambda_L = 15, lambda_C chosen from a short
+ *            Lanczos run, Chebyshev order 8, Krylov dimension
+ *            max(2 nv + 16, nv + 32), tolerance 1e-11 on ||(-Delta) v - lambda v||
+ *            relative to ||-Delta|| <= 12, at most 50 restarts).
+ *   report   optional (may be NULL).
+ * Returns LAPH_ERR_NOT_CONVERGED (outputs still written) if some pair misses
+ * the tolerance after max_restarts.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double lambda_L;      /* upper bound of the spectrum of -Delta (<= 0: 15)     */
+    double lambda_C;      /* cutoff mapped to 1 (<= 0: automatic)                 */
+    int cheb_order;       /* n of T_n (<= 0: 8)                                   */
+    int krylov_dim;       /* Krylov space dimension m (<= 0: automatic)           */
+    int max_restarts;     /* (<= 0: 50)                                           */
+    double tol;           /* residual tolerance relative to 12 (<= 0: 1e-11)      */
+    uint64_t seed;        /* start vector seed (0: the all-equal start vector)    */
+} laph_eig_params;
+
+typedef struct {
+    int restarts;         /* restarts performed                                   */
+    int matvecs;          /* Laplacian applications per slice                     */
+    int nconv;            /* minimum over slices of converged pairs               */
+    double max_resid;     /* max over slices/pairs of ||Lv - lambda v||           */
+    double lambda_C;      /* cutoff used                                          */
+} laph_eig_report;
+
+int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *links3d, int nv,
+                 const laph_eig_params *params, double *evals, void *evecs,
+                 laph_eig_report *report, void *stream);
+
+/* ------------------------------------------------------------------------
+ * (b) Z4 noise and diluted sources (Sec. II, Eq. (varrhodef) with D = 1 and
+ * the dilution projectors P^(b) = P_T (x) P_S (x) P_L; Sec. IV noise).
+ * Noise: rho(t, alpha, n) = i^v with v the low two bits of word 0 of
+ * Philox4x32-10(counter = ((t*4 + alpha)*nv + n, 0, 0, 0),
+ *               key = ((config_id << 16) | noise_id, 0x4C415048)).
+ * Dilution type codes per index space (N = nt, 4, nv): 0 none (1 projector),
+ * 1 full (N), 2 block-J (J; P^(b)_ii = [floor(J i / N) == b]),
+ * 3 interlace-J (J; P^(b)_ii = [i mod J == b]); N must be divisible by J.
+ * Flat projector index b = (b_T * n_S + b_S) * n_L + b_L.
+ *   b_list   nb projector indices to build (host or device int array).
+ *   rhs      [nb][V][4][3] c128 output: gamma_4 V_s P^(b) rho, i.e. the
+ *            right-hand side of K x = gamma_4 y for Omega x = y.
+ *   noise    optional [nt][4][nv] uint8 output of the codes v (may be NULL).
+ * Errors: LAPH_ERR_ARG for a bad dilution (J not dividing N) or b out of range.
+ * ------------------------------------------------------------------------ */
+typedef struct { int type; int J; } laph_dil1;
+typedef struct { laph_dil1 T, S, L; } laph_dilution;
+
+int laph_make_sources(laph_ctx *ctx, const laph_lattice *lat, const void *evecs, int nv,
+                      uint16_t noise_id, uint16_t config_id, const laph_dilution *dil,
+                      const int *b_list, int nb, void *rhs, uint8_t *noise, void *stream);
+
+/* ------------------------------------------------------------------------
+ * (c) Solves of K x = b for nrhs right-hand sides (Sec. II: Omega = gamma_4 K;
+ * Sec. IV: even-odd preconditioned BiCGStab, CG on the normal equations
+ * when it fails).  K is the anisotropic Wilson-clover matrix
+ *   K psi(x) = (m0 + 3/xi + 1) psi(x)
+ *     - 1/2 sum_mu w_mu [(1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)]
+ *     - (c_sw/2) sum_{mu<nu} w_{mu nu} sigma_{mu nu} F_{mu nu}(x) psi(x),
+ * w = 1/xi (space), 1 (time); w_{k4} = (1 + 1/xi)/2, w_{jk} = 1/xi; F the
+ * traceless clover-leaf field strength; sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu];
+ * periodic in space, antiperiodic in time for the fermion.
+ *   links  [V][4][3][3] c128 (the Dirac links, not the 3D-smeared ones).
+ *   rhs    [nrhs][V][4][3] c128 right-hand sides b.
+ *   sol    [nrhs][V][4][3] c128 solutions x (written).
+ *   params solver choice; NULL = MIXED_FP32, tol 1e-10.
+ *   report optional [nrhs] array.
+ * Convergence is judged by the FP64 true residual ||b - K x|| / ||b|| on the
+ * full (not even-odd) operator.  Modes:
+ *   LAPH_SOLVE_PLAIN_FP64  FP64 even-odd BiCGStab, rhs_block RHS per launch
+ *                          (rhs_block = 1 is the one-at-a-time baseline).
+ *   LAPH_SOLVE_MIXED_FP32  FP64 defect correction around FP32 even-odd
+ *                          BiCGStab, all RHS of a block in one launch.
+ *   LAPH_SOLVE_MIXED_BF16  as MIXED_FP32 with BF16 storage of the inner
+ *                          stencil operands (FP32 arithmetic).
+ *   LAPH_SOLVE_LEARNED     FP64 defect correction around FP32 flexible GCR
+ *                          with the learned right preconditioner `weights`
+ *                          (layout of laph_precond_train).
+ * A right-hand side that stalls (no 10x residual drop in 200 inner
+ * iterations, or BiCGStab breakdown) is finished by FP64 CG on K^dag K
+ * when params->fallback is nonzero; report[i].fallback_used is set.
+ * ------------------------------------------------------------------------ */
+enum {
+    LAPH_SOLVE_PLAIN_FP64 = 0,
+    LAPH_SOLVE_MIXED_FP32 = 1,
+    LAPH_SOLVE_MIXED_BF16 = 2,
+    LAPH_SOLVE_LEARNED = 3
+};
+
+typedef struct {
+    double m0;    /* bare mass                */
+    double csw;   /* clover coefficient       */
+} laph_dirac_params;
+
+typedef struct {
+    double tol;            /* FP64 true relative residual target (<= 0: 1e-10)     */
+    int maxiter;           /* total inner iterations per RHS (<= 0: 100000)        */
+    int mode;              /* LAPH_SOLVE_*                                          */
+    int rhs_block;         /* RHS per launch (<= 0: autotuned)                     */
+    double inner_tol;      /* inner relative tolerance per cycle (<= 0: 1e-5)      */
+    int fallback;          /* 1: CG on the normal equations after a stall          */
+    const float *weights;  /* LEARNED only: preconditioner weights (device/host)   */
+    int gcr_restart;       /* LEARNED only: FGCR restart length (<= 0: 16)         */
+    int check_every;       /* iterations between host convergence checks (<= 0: 25)*/
+} laph_solver_params;
+
+typedef struct {
+    int iters;             /* inner iterations (Schur-operator applications / 2)   */
+    int outer;             /* defect-correction cycles                              */
+    int status;            /* LAPH_OK or LAPH_ERR_NOT_CONVERGED                     */
+    int fallback_used;     /* 1 if the CG fallback ran                              */
+    double true_resid;     /* final ||b - K x|| / ||b|| in FP64                     */
+} laph_solve_report;
+
+int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const void *links,
+                      const laph_dirac_params *dirac, const void *rhs, void *sol, int nrhs,
+                      const laph_solver_params *params, laph_solve_report *report, void *stream);
+
+/* Applies K (FP64) to nrhs fields: out = K in (layouts as dirac_solve_batch). */
+int laph_dirac_apply(laph_ctx *ctx, const laph_lattice *lat, const void *links,
+                     const laph_dirac_params *dirac, const void *in, void *out, int nrhs,
+                     void *stream);
+
+/* ------------------------------------------------------------------------
+ * (d) Sink coefficients (Sec. IV: the quark-propagation coefficients
+ * V_s^dag Omega^{-1} V_s P^(b) rho, N_t N_v per spin):
+ *   coef[i][t][alpha][n] = sum_{x in slice t, c} conj(V(t,n,x,c)) sol[i](t,x,alpha,c)
+ *   evecs [nt][nv][V3][3], sol [nrhs][V][4][3], coef [nrhs][nt][4][nv], all c128.
+ * ------------------------------------------------------------------------ */
+int laph_sinks(laph_ctx *ctx, const laph_lattice *lat, const void *evecs, int nv,
+               const void *sol, int nrhs, void *coef, void *stream);
+
+/* ------------------------------------------------------------------------
+ * (d) Correlators in coefficient space (Sec. III, meson function
+ * Eq. (mesonfunc) at zero momentum without displacement, correlator
+ * Eq. (mesoncorr) first term, gamma_5-swapped line Eq. (laphpropg5)).
+ * With c = gamma_4 Gamma (q-bar = psi-bar gamma_4):
+ *   M^[b1 b2](a, b; t) = sum_n sum_{alpha beta} conj(a^[b1](t,alpha,n)) c_{alpha beta} b^[b2](t,beta,n)
+ *   meson:  C(dt) = - sum_{b1 b2} M(phibar_1, phi_2; t0+dt) conj(M(rhobar_1, rho_2; t0))
+ *   I=2 pi pi: C = Cpi(1,2) Cpi(3,4) - X,
+ *     X = sum M^[b1 b4](phibar_1, phi_4; tF) M^[b3 b2](phibar_3, phi_2; tF)
+ *               conj(M^[b1 b2](rhobar_1, rho_2; t0)) conj(M^[b3 b4](rhobar_3, rho_4; t0))
+ * where phi = coef, rho^[b] = P^(b) rho (LapH coordinates), phibar = gamma_5 gamma_4 phi,
+ * rhobar = -gamma_5 gamma_4 rho.  Channels: pion (Gamma = gamma_5), rho
+ * (gamma_k, the three averaged), scalar (1), I=2 pi pi.
+ *   spec->nlines quark lines (2 for mesons, 4 for pi pi); line k has
+ *   coef[k] = [nb][nt][4][nv] c128 (the sinks of its nb solved projectors,
+ *   in the order of b_list[k]) and noise[k] = [nt][4][nv] uint8 codes.
+ *   corr  [nt] c128 output, indexed by dt = (tF - t0) mod nt.
+ * All lines of one call share nb, b_list and the dilution scheme.
+ * ------------------------------------------------------------------------ */
+enum { LAPH_CH_PION = 0, LAPH_CH_RHO = 1, LAPH_CH_SCALAR = 2, LAPH_CH_PIPI_I2 = 3 };
+
+typedef struct {
+    int channel;              /* LAPH_CH_*                                          */
+    int t0;                   /* source time                                        */
+    int nv;
+    laph_dilution dil;        /* dilution of every line                             */
+    int nb;                   /* projectors per line                                */
+    const int *b_list;        /* [nb] flat projector indices (host)                 */
+} laph_corr_spec;
+
+int correlate(laph_ctx *ctx, const laph_lattice *lat, const laph_corr_spec *spec,
+              const void *const *coef, const uint8_t *const *noise, void *corr, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAPH_H */

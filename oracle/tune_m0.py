@@ -30,11 +30,11 @@ def _count(args):
     wl = synth.WORKLOADS[wl_name]
     b = synth.random_spinor(wl.ns, wl.nt, seed=99)
     fk = FastK(WilsonClover(u, m0, wl.csw, wl.xi))
-    x, it, rr = fk.solve(b, tol=1e-10, maxiter=50000, nthreads=1)
+    x, it, rr = fk.solve(b, tol=1e-10, maxiter=4 * wl.target_iters, nthreads=1)
     return m0, it, rr
 
 
-def tune(name, lo=-0.16, hi=0.0, passes=3, width=8):
+def tune(name, lo=-0.16, hi=0.04, passes=3, width=8):
     from oracle import gauge
     wl = synth.WORKLOADS[name]
     u, _ = gauge.prepare_links(wl.gauge(), wl.rho_stout, wl.n_stout4d, 0)

@@ -1,0 +1,307 @@
+// Multi-RHS BLAS-1 kernels and the per-RHS BiCGStab scalar updates.
+#include <cmath>
+
+#include "blas.cuh"
+
+namespace laph {
+
+RedPlan red_plan(laph_ctx *ctx, long nrows, int nr) {
+    LAPH_REQUIRE(nr >= 1 && nr <= 256, "right-hand-side block must be 1..256");
+    RedPlan p;
+    p.nr = nr;
+    p.rpb = 1;
+    while (nr * p.rpb * 2 <= 256) p.rpb *= 2;
+    p.block = nr * p.rpb;
+    long want = (nrows + p.rpb - 1) / p.rpb;
+    long cap = 4L * (ctx->sm_count > 0 ? ctx->sm_count : 152);
+    p.grid = (unsigned)(want < cap ? (want < 1 ? 1 : want) : cap);
+    return p;
+}
+
+// ------------------------------------------------------------------ reductions
+template <int NRED, class Body>
+__global__ void red_kernel(long nrows, int nr, int rpb, Body body, c64 *partial) {
+    extern __shared__ c64 sm[];
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const int r = tid % nr, row0 = tid / nr;
+    c64 acc[NRED];
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) acc[k] = {0.0, 0.0};
+    for (long row = (long)blockIdx.x * rpb + row0; row < nrows; row += (long)gridDim.x * rpb)
+        body(row * nr + r, r, acc);
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) sm[k * bd + tid] = acc[k];
+    __syncthreads();
+    for (int st = rpb / 2; st > 0; st >>= 1) {
+        if (row0 < st)
+#pragma unroll
+            for (int k = 0; k < NRED; ++k) sm[k * bd + tid] += sm[k * bd + tid + st * nr];
+        __syncthreads();
+    }
+    if (row0 == 0)
+#pragma unroll
+        for (int k = 0; k < NRED; ++k) partial[((long)blockIdx.x * NRED + k) * nr + r] = sm[k * bd + r];
+}
+
+// out[k][r] = sum_b partial[b][k][r], one block per (k, r), fixed order.
+__global__ void red_final(const c64 *partial, int nblk, int nred, int nr, c64 *out) {
+    __shared__ c64 sm[256];
+    int kr = blockIdx.x;
+    int k = kr / nr, r = kr % nr;
+    c64 a{0.0, 0.0};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) a += partial[((long)b * nred + k) * nr + r];
+    sm[threadIdx.x] = a;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k * nr + r] = sm[0];
+}
+
+template <int NRED, class Body>
+static void run_reduce(laph_ctx *ctx, const RedPlan &pl, long nrows, const Body &body, c64 *out, cudaStream_t s) {
+    c64 *partial = (c64 *)ws_get(ctx, "red:partial", sizeof(c64) * pl.grid * NRED * pl.nr);
+    size_t shm = sizeof(c64) * NRED * pl.block;
+    red_kernel<NRED, Body><<<pl.grid, pl.block, shm, s>>>(nrows, pl.nr, pl.rpb, body, partial);
+    LAPH_LAUNCH_CHECK();
+    red_final<<<NRED * pl.nr, 256, 0, s>>>(partial, (int)pl.grid, NRED, pl.nr, out);
+    LAPH_LAUNCH_CHECK();
+}
+
+template <typename T>
+struct Dots1 {
+    const cpx<T> *a0, *b0;
+    __device__ void operator()(long i, int, c64 *acc) const { acc[0] += cmul_conj(cvt<double>(a0[i]), cvt<double>(b0[i])); }
+};
+template <typename T>
+struct Dots2 {
+    const cpx<T> *a0, *b0, *a1, *b1;
+    __device__ void operator()(long i, int, c64 *acc) const {
+        acc[0] += cmul_conj(cvt<double>(a0[i]), cvt<double>(b0[i]));
+        acc[1] += cmul_conj(cvt<double>(a1[i]), cvt<double>(b1[i]));
+    }
+};
+template <typename T>
+struct Dots3 {
+    const cpx<T> *a0, *b0, *a1, *b1, *a2, *b2;
+    __device__ void operator()(long i, int, c64 *acc) const {
+        acc[0] += cmul_conj(cvt<double>(a0[i]), cvt<double>(b0[i]));
+        acc[1] += cmul_conj(cvt<double>(a1[i]), cvt<double>(b1[i]));
+        acc[2] += cmul_conj(cvt<double>(a2[i]), cvt<double>(b2[i]));
+    }
+};
+
+template <typename T>
+void mrhs_dots(laph_ctx *ctx, const RedPlan &pl, long nrows, int nred, const cpx<T> *a0, const cpx<T> *b0,
+               const cpx<T> *a1, const cpx<T> *b1, const cpx<T> *a2, const cpx<T> *b2, c64 *out, cudaStream_t s) {
+    if (nred == 1)
+        run_reduce<1>(ctx, pl, nrows, Dots1<T>{a0, b0}, out, s);
+    else if (nred == 2)
+        run_reduce<2>(ctx, pl, nrows, Dots2<T>{a0, b0, a1, b1}, out, s);
+    else
+        run_reduce<3>(ctx, pl, nrows, Dots3<T>{a0, b0, a1, b1, a2, b2}, out, s);
+}
+template void mrhs_dots<float>(laph_ctx *, const RedPlan &, long, int, const c32 *, const c32 *, const c32 *,
+                               const c32 *, const c32 *, const c32 *, c64 *, cudaStream_t);
+template void mrhs_dots<double>(laph_ctx *, const RedPlan &, long, int, const c64 *, const c64 *, const c64 *,
+                                const c64 *, const c64 *, const c64 *, c64 *, cudaStream_t);
+
+// ------------------------------------------------------------------ elementwise
+template <typename Tx, typename Ty>
+__global__ void axpy_scaled_kernel(long n, int nr, const double *scale, const cpx<Tx> *x, cpx<Ty> *y) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a = scale[i % nr];
+    cpx<double> v = cvt<double>(y[i]) + a * cvt<double>(x[i]);
+    y[i] = cvt<Ty>(v);
+}
+
+template <typename Tx, typename Ty>
+void mrhs_axpy_scaled(long nrows, int nr, const double *scale, const cpx<Tx> *x, cpx<Ty> *y, cudaStream_t s) {
+    long n = nrows * nr;
+    axpy_scaled_kernel<Tx, Ty><<<grid_for(n, 256), 256, 0, s>>>(n, nr, scale, x, y);
+    LAPH_LAUNCH_CHECK();
+}
+template void mrhs_axpy_scaled<float, double>(long, int, const double *, const c32 *, c64 *, cudaStream_t);
+template void mrhs_axpy_scaled<double, double>(long, int, const double *, const c64 *, c64 *, cudaStream_t);
+
+template <typename Tx, typename Ty>
+__global__ void copy_scaled_kernel(long n, int nr, const double *scale, const cpx<Tx> *x, cpx<Ty> *y) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a = scale[i % nr];
+    y[i] = cvt<Ty>(a * cvt<double>(x[i]));
+}
+
+template <typename Tx, typename Ty>
+void mrhs_copy_scaled(long nrows, int nr, const double *scale, const cpx<Tx> *x, cpx<Ty> *y, cudaStream_t s) {
+    long n = nrows * nr;
+    copy_scaled_kernel<Tx, Ty><<<grid_for(n, 256), 256, 0, s>>>(n, nr, scale, x, y);
+    LAPH_LAUNCH_CHECK();
+}
+template void mrhs_copy_scaled<double, float>(long, int, const double *, const c64 *, c32 *, cudaStream_t);
+template void mrhs_copy_scaled<double, double>(long, int, const double *, const c64 *, c64 *, cudaStream_t);
+
+__global__ void sub_kernel(long n, const c64 *x, const c64 *y, c64 *z) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) z[i] = x[i] - y[i];
+}
+void mrhs_sub(long n, const c64 *x, const c64 *y, c64 *z, cudaStream_t s) {
+    sub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, x, y, z);
+    LAPH_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ BiCGStab pieces
+template <typename T>
+__global__ void p_update_kernel(long n, int nr, BicgScalars sc, const cpx<T> *r, cpx<T> *p, const cpx<T> *v) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = (int)(i % nr);
+    cpx<T> b = cvt<T>(sc.beta[k]), w = cvt<T>(sc.omega[k]);
+    cpx<T> bp = p[i] - w * v[i];
+    p[i] = r[i] + b * bp;
+}
+template <typename T>
+void bicg_p_update(long nrows, int nr, const BicgScalars &sc, const cpx<T> *r, cpx<T> *p, const cpx<T> *v,
+                   cudaStream_t s) {
+    long n = nrows * nr;
+    p_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(n, nr, sc, r, p, v);
+    LAPH_LAUNCH_CHECK();
+}
+
+template <typename T>
+__global__ void s_update_kernel(long n, int nr, BicgScalars sc, const cpx<T> *r, const cpx<T> *v, cpx<T> *sv) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    cpx<T> a = cvt<T>(sc.alpha[i % nr]);
+    sv[i] = r[i] - a * v[i];
+}
+template <typename T>
+void bicg_s_update(long nrows, int nr, const BicgScalars &sc, const cpx<T> *r, const cpx<T> *v, cpx<T> *sv,
+                   cudaStream_t s) {
+    long n = nrows * nr;
+    s_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(n, nr, sc, r, v, sv);
+    LAPH_LAUNCH_CHECK();
+}
+
+template <typename T>
+struct XRBody {
+    BicgScalars sc;
+    cpx<T> *x;
+    const cpx<T> *p, *sv, *t;
+    cpx<T> *r;
+    const cpx<T> *rhat;
+    __device__ void operator()(long i, int k, c64 *acc) const {
+        cpx<T> a = cvt<T>(sc.alpha[k]), w = cvt<T>(sc.omega[k]);
+        x[i] = x[i] + a * p[i] + w * sv[i];
+        cpx<T> rn = sv[i] - w * t[i];
+        r[i] = rn;
+        acc[0] += cmul_conj(cvt<double>(rhat[i]), cvt<double>(rn));
+        acc[1] += cvt<double>(cmul_conj(rn, rn));
+    }
+};
+
+template <typename T>
+void bicg_xr_update_reduce(laph_ctx *ctx, const RedPlan &pl, long nrows, const BicgScalars &sc, cpx<T> *x,
+                           const cpx<T> *p, const cpx<T> *sv, const cpx<T> *t, cpx<T> *r, const cpx<T> *rhat,
+                           c64 *red, cudaStream_t s) {
+    run_reduce<2>(ctx, pl, nrows, XRBody<T>{sc, x, p, sv, t, r, rhat}, red, s);
+}
+
+template void bicg_p_update<float>(long, int, const BicgScalars &, const c32 *, c32 *, const c32 *, cudaStream_t);
+template void bicg_p_update<double>(long, int, const BicgScalars &, const c64 *, c64 *, const c64 *, cudaStream_t);
+template void bicg_s_update<float>(long, int, const BicgScalars &, const c32 *, const c32 *, c32 *, cudaStream_t);
+template void bicg_s_update<double>(long, int, const BicgScalars &, const c64 *, const c64 *, c64 *, cudaStream_t);
+template void bicg_xr_update_reduce<float>(laph_ctx *, const RedPlan &, long, const BicgScalars &, c32 *, const c32 *,
+                                           const c32 *, const c32 *, c32 *, const c32 *, c64 *, cudaStream_t);
+template void bicg_xr_update_reduce<double>(laph_ctx *, const RedPlan &, long, const BicgScalars &, c64 *, const c64 *,
+                                            const c64 *, const c64 *, c64 *, const c64 *, c64 *, cudaStream_t);
+
+__device__ __forceinline__ c64 cdiv(c64 a, c64 b) {
+    double d = norm2(b);
+    return c64{(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+
+__device__ __forceinline__ void deactivate(const BicgScalars &sc, int k, int status) {
+    sc.active[k] = 0;
+    sc.status[k] = status;
+    sc.alpha[k] = c64{0.0, 0.0};
+    sc.omega[k] = c64{0.0, 0.0};
+    sc.beta[k] = c64{0.0, 0.0};
+}
+
+__global__ void init_scalars_kernel(int nr, BicgScalars sc, const c64 *red_rr, double rel_tol) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr) return;
+    double rr = red_rr[k].re;
+    sc.rho[k] = c64{rr, 0.0};   // <rhat, r> with rhat = r
+    sc.alpha[k] = c64{1.0, 0.0};
+    sc.omega[k] = c64{1.0, 0.0};
+    sc.beta[k] = c64{rr, 0.0};  // (rho / rho_old)(alpha / omega) with rho_old = 1: p = r first
+    sc.rr[k] = rr;
+    sc.rr_stop[k] = rel_tol * rel_tol * rr;
+    sc.iters[k] = 0;
+    bool run = rr > 0.0 && isfinite(rr);
+    sc.active[k] = run ? 1 : 0;
+    sc.status[k] = run ? 0 : 1;
+    if (!run) deactivate(sc, k, 1);
+}
+void bicg_init_scalars(int nr, const BicgScalars &sc, const c64 *red_rr, double rel_tol, cudaStream_t s) {
+    init_scalars_kernel<<<grid_for(nr, 64), 64, 0, s>>>(nr, sc, red_rr, rel_tol);
+    LAPH_LAUNCH_CHECK();
+}
+
+// alpha = rho / <rhat, v>
+__global__ void alpha_kernel(int nr, BicgScalars sc, const c64 *red) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr || !sc.active[k]) return;
+    sc.iters[k] += 1;
+    c64 d = red[k];
+    double dn = norm2(d);
+    if (!(dn > 0.0) || !isfinite(dn) || dn < 1e-60 * sc.rr[k] * sc.rr[k]) { deactivate(sc, k, 2); return; }
+    sc.alpha[k] = cdiv(sc.rho[k], d);
+}
+void bicg_alpha(int nr, const BicgScalars &sc, const c64 *red, cudaStream_t s) {
+    alpha_kernel<<<grid_for(nr, 64), 64, 0, s>>>(nr, sc, red);
+    LAPH_LAUNCH_CHECK();
+}
+
+// omega = <t, s> / <t, t>
+__global__ void omega_kernel(int nr, BicgScalars sc, const c64 *red) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr || !sc.active[k]) return;
+    c64 ts = red[k];
+    double tt = red[nr + k].re;
+    if (!(tt > 0.0) || !isfinite(tt)) {
+        // t = M s = 0 means s = 0: the half step already solved the system
+        sc.omega[k] = c64{0.0, 0.0};
+        return;
+    }
+    sc.omega[k] = c64{ts.re / tt, ts.im / tt};
+}
+void bicg_omega(int nr, const BicgScalars &sc, const c64 *red, cudaStream_t s) {
+    omega_kernel<<<grid_for(nr, 64), 64, 0, s>>>(nr, sc, red);
+    LAPH_LAUNCH_CHECK();
+}
+
+// rho_new = <rhat, r>, rr = <r, r>; beta = (rho_new / rho)(alpha / omega); convergence test
+__global__ void rho_kernel(int nr, BicgScalars sc, const c64 *red) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr || !sc.active[k]) return;
+    c64 rn = red[k];
+    double rr = red[nr + k].re;
+    sc.rr[k] = rr;
+    if (!isfinite(rr) || !isfinite(rn.re) || !isfinite(rn.im)) { deactivate(sc, k, 2); return; }
+    if (rr <= sc.rr_stop[k]) { deactivate(sc, k, 1); return; }
+    c64 w = sc.omega[k];
+    if (norm2(w) == 0.0 || norm2(rn) == 0.0) { deactivate(sc, k, 2); return; }
+    sc.beta[k] = cdiv(rn, sc.rho[k]) * cdiv(sc.alpha[k], w);
+    sc.rho[k] = rn;
+}
+void bicg_rho(int nr, const BicgScalars &sc, const c64 *red, cudaStream_t s) {
+    rho_kernel<<<grid_for(nr, 64), 64, 0, s>>>(nr, sc, red);
+    LAPH_LAUNCH_CHECK();
+}
+
+}  // namespace laph

@@ -1,0 +1,219 @@
+"""Python binding of liblaph (include/laph.h): argument marshalling only.
+
+Every function has the name of its C entry point and forwards to it through
+ctypes.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays; complex128
+arrays are passed as interleaved doubles.  The work runs in the CUDA library:
+if liblaph.so is missing this module raises on import, there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+if not os.path.exists(LIB):
+    raise ImportError(f"{LIB} is not built; run paper_1104_3870_gb300.build.build() (needs nvcc)")
+
+_lib = ctypes.CDLL(LIB)
+
+LAPH_OK, LAPH_ERR_ARG, LAPH_ERR_CUDA, LAPH_ERR_NOT_CONVERGED, LAPH_ERR_TIMEOUT, LAPH_ERR_NOMEM = range(6)
+PLAIN_FP64, MIXED_FP32, MIXED_BF16, LEARNED = range(4)
+CH_PION, CH_RHO, CH_SCALAR, CH_PIPI_I2 = range(4)
+DIL_NONE, DIL_FULL, DIL_BLOCK, DIL_INTERLACE = range(4)
+
+
+class LaphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"liblaph error {code}: {msg}")
+        self.code = code
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_int), ("nt", ctypes.c_int), ("xi", ctypes.c_double)]
+
+
+class DiracParams(ctypes.Structure):
+    _fields_ = [("m0", ctypes.c_double), ("csw", ctypes.c_double)]
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("mode", ctypes.c_int),
+                ("rhs_block", ctypes.c_int), ("inner_tol", ctypes.c_double), ("fallback", ctypes.c_int),
+                ("weights", ctypes.c_void_p), ("gcr_restart", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("status", ctypes.c_int),
+                ("fallback_used", ctypes.c_int), ("true_resid", ctypes.c_double)]
+
+
+class EigParams(ctypes.Structure):
+    _fields_ = [("lambda_L", ctypes.c_double), ("lambda_C", ctypes.c_double), ("cheb_order", ctypes.c_int),
+                ("krylov_dim", ctypes.c_int), ("max_restarts", ctypes.c_int), ("tol", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class EigReport(ctypes.Structure):
+    _fields_ = [("restarts", ctypes.c_int), ("matvecs", ctypes.c_int), ("nconv", ctypes.c_int),
+                ("max_resid", ctypes.c_double), ("lambda_C", ctypes.c_double)]
+
+
+class Dil1(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("J", ctypes.c_int)]
+
+
+class Dilution(ctypes.Structure):
+    _fields_ = [("T", Dil1), ("S", Dil1), ("L", Dil1)]
+
+
+class CorrSpec(ctypes.Structure):
+    _fields_ = [("channel", ctypes.c_int), ("t0", ctypes.c_int), ("nv", ctypes.c_int), ("dil", Dilution),
+                ("nb", ctypes.c_int), ("b_list", ctypes.POINTER(ctypes.c_int))]
+
+
+_vp = ctypes.c_void_p
+_sig = {
+    "laph_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp)]),
+    "laph_ctx_destroy": (None, [_vp]),
+    "laph_last_error": (ctypes.c_char_p, []),
+    "laph_version": (ctypes.c_char_p, []),
+    "laph_stout_smear": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_int, _vp]),
+    "laph_eigvecs": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, ctypes.POINTER(EigParams),
+                                    _vp, _vp, ctypes.POINTER(EigReport), _vp]),
+    "laph_make_sources": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, ctypes.c_uint16,
+                                         ctypes.c_uint16, ctypes.POINTER(Dilution), _vp, ctypes.c_int, _vp, _vp,
+                                         _vp]),
+    "dirac_solve_batch": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), _vp, _vp,
+                                         ctypes.c_int, ctypes.POINTER(SolverParams), _vp, _vp]),
+    "laph_dirac_apply": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), _vp, _vp,
+                                        ctypes.c_int, _vp]),
+    "laph_sinks": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
+    "correlate": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    if hasattr(_lib, _name):
+        f = getattr(_lib, _name)
+        f.restype = _res
+        f.argtypes = _args
+
+
+def exported_symbols():
+    return [n for n in _sig if hasattr(_lib, n)]
+
+
+def _check(rc, allow=()):
+    if rc != LAPH_OK and rc not in allow:
+        raise LaphError(rc, _lib.laph_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays passed to liblaph must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors passed to liblaph must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def lattice(ns, nt, xi):
+    return Lattice(int(ns), int(nt), float(xi))
+
+
+def dilution(T, S, L):
+    return Dilution(Dil1(*T), Dil1(*S), Dil1(*L))
+
+
+class Context:
+    """Owns a laph_ctx (device workspace, autotune cache)."""
+
+    def __init__(self, device=0):
+        self.ptr = _vp()
+        _check(_lib.laph_ctx_create(int(device), ctypes.byref(self.ptr)))
+
+    def close(self):
+        if self.ptr:
+            _lib.laph_ctx_destroy(self.ptr)
+            self.ptr = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version():
+    return _lib.laph_version().decode()
+
+
+def laph_stout_smear(ctx, lat, links, rho, nsteps, spatial_only, stream=None):
+    _check(_lib.laph_stout_smear(ctx.ptr, ctypes.byref(lat), _ptr(links), float(rho), int(nsteps),
+                                 int(spatial_only), _stream(stream)))
+
+
+def laph_eigvecs(ctx, lat, links3d, nv, evals, evecs, params=None, stream=None, allow_not_converged=False):
+    rep = EigReport()
+    rc = _lib.laph_eigvecs(ctx.ptr, ctypes.byref(lat), _ptr(links3d), int(nv),
+                           ctypes.byref(params) if params is not None else None, _ptr(evals), _ptr(evecs),
+                           ctypes.byref(rep), _stream(stream))
+    _check(rc, allow=(LAPH_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return rep
+
+
+def laph_make_sources(ctx, lat, evecs, nv, noise_id, config_id, dil, b_list, rhs, noise=None, stream=None):
+    b = np.ascontiguousarray(np.asarray(b_list, dtype=np.int32))
+    _check(_lib.laph_make_sources(ctx.ptr, ctypes.byref(lat), _ptr(evecs), int(nv), int(noise_id), int(config_id),
+                                  ctypes.byref(dil), b.ctypes.data, len(b), _ptr(rhs), _ptr(noise),
+                                  _stream(stream)))
+
+
+def solver_params(tol=1e-10, maxiter=100000, mode=MIXED_FP32, rhs_block=0, inner_tol=0.0, fallback=1,
+                  weights=None, gcr_restart=16, check_every=25):
+    return SolverParams(tol, maxiter, mode, rhs_block, inner_tol, fallback, _ptr(weights), gcr_restart, check_every)
+
+
+def dirac_solve_batch(ctx, lat, links, m0, csw, rhs, sol, nrhs, params=None, stream=None, allow_not_converged=False):
+    reps = (SolveReport * max(nrhs, 1))()
+    prm = params if params is not None else solver_params()
+    rc = _lib.dirac_solve_batch(ctx.ptr, ctypes.byref(lat), _ptr(links), ctypes.byref(DiracParams(m0, csw)),
+                                _ptr(rhs), _ptr(sol), int(nrhs), ctypes.byref(prm), reps, _stream(stream))
+    _check(rc, allow=(LAPH_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return [reps[i] for i in range(nrhs)]
+
+
+def laph_dirac_apply(ctx, lat, links, m0, csw, inp, out, nrhs, stream=None):
+    _check(_lib.laph_dirac_apply(ctx.ptr, ctypes.byref(lat), _ptr(links), ctypes.byref(DiracParams(m0, csw)),
+                                 _ptr(inp), _ptr(out), int(nrhs), _stream(stream)))
+
+
+def laph_sinks(ctx, lat, evecs, nv, sol, nrhs, coef, stream=None):
+    _check(_lib.laph_sinks(ctx.ptr, ctypes.byref(lat), _ptr(evecs), int(nv), _ptr(sol), int(nrhs), _ptr(coef),
+                           _stream(stream)))
+
+
+def correlate(ctx, lat, channel, t0, nv, dil, b_list, coefs, noises, corr, stream=None):
+    b = np.ascontiguousarray(np.asarray(b_list, dtype=np.int32))
+    spec = CorrSpec(int(channel), int(t0), int(nv), dil, len(b), b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    cp = (_vp * len(coefs))(*[_ptr(c) for c in coefs])
+    npt = (_vp * len(noises))(*[_ptr(n) for n in noises])
+    _check(_lib.correlate(ctx.ptr, ctypes.byref(lat), ctypes.byref(spec), cp, npt, _ptr(corr), _stream(stream)))

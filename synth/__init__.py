@@ -116,7 +116,7 @@ class Workload:
 
 WORKLOADS = {
     # 4^3x8, N_v = 8, full time/spin/LapH dilution (the exact case).
-    "tiny_4x8": Workload("tiny_4x8", ns=4, nt=8, xi=3.5, csw=1.0, m0=-0.08305, nv=8,
+    "tiny_4x8": Workload("tiny_4x8", ns=4, nt=8, xi=3.5, csw=1.0, m0=-0.04898, nv=8,
                          gauge_seed=1000, dil_time=(DIL_FULL, 0), dil_spin=(DIL_FULL, 0),
                          dil_laph=(DIL_FULL, 0), source_times=tuple(range(8)), n_noise=2,
                          target_iters=150),
