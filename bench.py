@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the stochastic-LapH quark-line path on GB300.
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+Laplacian eigenvectors of every slice (a1), Z4 diluted sources for two noises
+(a2), the batched solves of all diluted sources to FP64 true residual 1e-10
+(a3), sink coefficients (a4) and the pion / scalar / rho correlators (a5).
+Gauge preparation (stout smearing, a0) is setup and not timed.
+
+Default workload: 16^3 x 32, xi = 3.5, N_v = 32, (TF, SF, LI8) at t0 = 0, two
+noises -> 64 diluted sources per step (seeded synthetic gauge field).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+replica (its own noises); value = sources of all ranks / max rank time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "diluted LapH sources solved/s at resid 1e-10, learned vs plain; Dslash HBM GB/s"
+UNIT = "sources/s"
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="medium_16x32")
+    p.add_argument("--mode", choices=["mixed", "plain"], default="mixed")
+    p.add_argument("--plain-sample", type=int, default=2, help="sources solved by the plain FP64 comparison")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- distribution
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate_max(value, world, device=None):
+    """Max of a float over ranks (barrier included); identity for one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def whole_job_rate(units_per_rank, world, max_seconds):
+    return units_per_rank * world / max_seconds
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(wl, seconds=15.0, threads=None):
+    """Times the oracle's plain-C BiCGStab (oracle/c/oracle_dirac.c, one solve per
+    thread) for a bounded number of iterations and scales to sources/s with the
+    iteration count a full solve needs at this m0 (oracle/m0_tuned.json)."""
+    from oracle.dirac import WilsonClover
+    from oracle.fast import FastK
+    import synth
+    cores = threads or os.cpu_count() or 1
+    # iteration timing does not depend on the link values; unsmeared seeded links suffice
+    u0 = wl.gauge()
+    fk = FastK(WilsonClover(u0, wl.m0, wl.csw, wl.xi))
+    b = synth.random_spinor(wl.ns, wl.nt, seed=7, nrhs=cores)
+    t = time.perf_counter()
+    fk.solve(b[:1], tol=1e-30, maxiter=4, nthreads=1)
+    per_iter = (time.perf_counter() - t) / 4.0
+    tuned = os.path.join(ROOT, "oracle", "m0_tuned.json")
+    need = wl.target_iters
+    if os.path.exists(tuned):
+        rec = json.load(open(tuned)).get(wl.name)
+        if rec:
+            need = rec["iters"]
+    # stay below the length of a full solve so every thread runs exactly `iters` iterations
+    iters = max(4, min(int(seconds / max(per_iter, 1e-6)), need // 2))
+    t = time.perf_counter()
+    _, its, _ = fk.solve(b, tol=1e-30, maxiter=iters, nthreads=cores)
+    wall = time.perf_counter() - t
+    iters = int(np.mean(its))
+    rate = cores / (wall * need / iters)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} concurrent single-thread oracle BiCGStab solves (plain C, full operator) run for "
+                      f"{iters} iterations in {wall:.1f} s, scaled to the {need} iterations a solve to 1e-10 takes "
+                      f"at this m0; eigenvectors, sources, sinks and contractions not included"}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1104_3870_gb300 import build
+    build.build()
+    from paper_1104_3870_gb300 import laph as L
+    from paper_1104_3870_gb300.pipeline import LapHPath, LatticeSpec, projectors_for_time
+    import synth
+
+    wl = synth.WORKLOADS[args.workload]
+    spec = LatticeSpec(wl.ns, wl.nt, wl.xi, wl.m0, wl.csw, wl.nv, (wl.dil_time, wl.dil_spin, wl.dil_laph),
+                       wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
+    path = LapHPath(spec, local)
+    u, ut = path.prepare_links(wl.gauge())          # a0: setup, not timed
+    t0 = wl.source_times[0]
+    bs = projectors_for_time(spec, t0)
+    nb, nnoise = len(bs), wl.n_noise
+    nsrc = nb * nnoise
+    noise_ids = [rank * nnoise + k for k in range(nnoise)]
+    mode = L.MIXED_FP32 if args.mode == "mixed" else L.PLAIN_FP64
+    rhs = path.field(nsrc)
+    sol = torch.empty_like(rhs)
+    coef = torch.empty((nsrc, wl.nt, 4, wl.nv), dtype=torch.complex128, device="cuda")
+    codes = torch.empty((nnoise, wl.nt, 4, wl.nv), dtype=torch.uint8, device="cuda")
+    evals = torch.empty((wl.nt, wl.nv), dtype=torch.float64, device="cuda")
+    evecs = torch.empty((wl.nt, wl.nv, wl.ns ** 3, 3), dtype=torch.complex128, device="cuda")
+    channels = [L.CH_PION, L.CH_SCALAR, L.CH_RHO]
+    corr = torch.empty((len(channels), wl.nt), dtype=torch.complex128, device="cuda")
+    corr_host = torch.empty_like(corr, device="cpu").pin_memory()
+    stats = {}
+
+    def step(u_in, ut_in, read_back=False):
+        _, _, rep = path.eigvecs(ut_in, evals, evecs)
+        for k in range(nnoise):
+            path.sources(evecs, noise_ids[k], wl.config_id, bs, out=rhs[k * nb:(k + 1) * nb], codes=codes[k])
+        _, reps = path.solve(u_in, rhs, mode=mode, sol=sol)
+        path.sinks(evecs, sol, out=coef)
+        for i, ch in enumerate(channels):
+            path.correlate(ch, t0, bs, [coef[0:nb], coef[nb:2 * nb]], [codes[0], codes[1]], out=corr[i])
+        if read_back:
+            corr_host.copy_(corr, non_blocking=True)
+        stats["iters"] = [r.iters for r in reps]
+        stats["resid"] = max(r.true_resid for r in reps)
+        stats["eig"] = (rep.restarts, rep.matvecs, rep.max_resid)
+
+    for _ in range(args.warmup):
+        step(u, ut)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local) if rank == 0 else None
+    L.laph_profile_reset()
+    L.laph_profile_enable(True)
+    launches0 = L.laph_launch_count()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(u, ut)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = L.laph_launch_count() - launches0
+    L.laph_profile_enable(False)
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = aggregate_max(ms, world, device="cuda")
+    barrier(world)
+    value = whole_job_rate(nsrc, world, ms_max / 1000.0)
+    n32, ms32, by32, fl32 = L.laph_profile_read("dslash_fp32")
+    n64, ms64, by64, fl64 = L.laph_profile_read("dslash_fp64")
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if mode == L.MIXED_FP32 and n32:
+        fam, n, kms, kbytes = "dslash_fp32 (hop_kernel<float>)", n32, ms32, by32
+    else:
+        fam, n, kms, kbytes = "dslash_fp64 (hop_kernel<double>)", n64, ms64, by64
+    achieved = kbytes / (kms / 1000.0) / 1e9 if kms else None
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    traffic = None
+    if os.path.exists(traffic_file):
+        tr = json.load(open(traffic_file))
+        if tr.get("kernel_version") == "hop_v1" and tr.get("workload") == wl.name:
+            traffic = tr.get("bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
+                "kernel": fam, "launches": n, "avg_launch_us": 1000.0 * kms / n if n else None,
+                "algorithmic_bytes_per_launch": kbytes / n if n else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+
+    # e2e through the public API with host buffers: links in pinned host memory are staged by the
+    # library each call; the correlators are read back to host.
+    u_h = u.cpu().pin_memory()
+    ut_h = ut.cpu().pin_memory()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step(u_h, ut_h, read_back=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t) / args.e2e_steps
+    e2e_s = aggregate_max(e2e_s, world, device="cuda")
+    e2e = {"value": whole_job_rate(nsrc, world, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": int(u_h.numel() * u_h.element_size() * 2),
+           "d2h_bytes_per_step": int(corr_host.numel() * corr_host.element_size())}
+
+    # plain FP64 comparison on a sample of the same sources: one right-hand side per launch
+    variants = {}
+    if args.plain_sample > 0 and mode == L.MIXED_FP32:
+        sub = rhs[:args.plain_sample].clone()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        _, preps = path.solve(u, sub, mode=L.PLAIN_FP64, rhs_block=1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = ev0.elapsed_time(ev1)
+        variants["plain_fp64_one_rhs"] = {"sources_per_s": args.plain_sample / (ms_plain / 1000.0),
+                                          "iters": [r.iters for r in preps], "sample": args.plain_sample,
+                                          "true_resid_max": max(r.true_resid for r in preps)}
+    solve_only = None
+    if mode == L.MIXED_FP32:
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        _, sreps = path.solve(u, rhs, mode=L.MIXED_FP32, sol=sol)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        solve_only = nsrc / (ev0.elapsed_time(ev1) / 1000.0)
+        variants["mixed_fp32_batched_solve_only"] = {"sources_per_s": solve_only, "rhs_block": min(nsrc, 64),
+                                                     "iters_max": max(r.iters for r in sreps)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64" if mode == L.MIXED_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": f"{wl.name}: {wl.ns}^3x{wl.nt}, xi={wl.xi}, N_v={wl.nv}, dilution (TF,SF,LI8) "
+                                   f"at t0={t0}, {nnoise} noises x {nb} projectors per replica",
+                       "sources_per_step": nsrc, "solver": args.mode, "tol": 1e-10,
+                       "l2": "inputs larger than L2 (solver working set > 1 GB)", "parallelism": f"replicas{world}"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "variants": variants,
+            "path_stats": {"true_resid_max": stats.get("resid"), "inner_iters_max": max(stats.get("iters", [0])),
+                           "eig_restarts_matvecs_resid": stats.get("eig")}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(wl)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    path.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import synth
+    wl = synth.WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(wl, seconds=4.0)
+    vals = []
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(wl, seconds=8.0))
+    wall = (time.perf_counter() - t) / args.steps
+    v = float(np.mean([x["value"] for x in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * wall, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "sources_per_step": "bounded sample", "solver": "oracle BiCGStab"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

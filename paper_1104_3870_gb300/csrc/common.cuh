@@ -34,7 +34,19 @@ void set_last_error(const std::string &msg);
                                                   __FILE__ + ":" + std::to_string(__LINE__)); \
     } while (0)
 
-#define LAPH_LAUNCH_CHECK() LAPH_CUDA(cudaGetLastError())
+// Every kernel launch of the library is followed by this check; it also counts launches.
+void count_launch();
+#define LAPH_LAUNCH_CHECK()              \
+    do {                                 \
+        ::laph::count_launch();          \
+        LAPH_CUDA(cudaGetLastError());   \
+    } while (0)
+
+// Optional per-kernel-family timing with CUDA events on the launching stream
+// (enabled by laph_profile_enable); `bytes` is the algorithmic traffic of the launch.
+bool prof_on();
+void prof_begin(const char *family, cudaStream_t s);
+void prof_end(const char *family, cudaStream_t s, double bytes, double flops);
 
 #define LAPH_REQUIRE(cond, msg)                                                            \
     do {                                                                                   \

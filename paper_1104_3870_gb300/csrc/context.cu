@@ -1,5 +1,8 @@
-// Context, workspace, host/device staging and error reporting of liblaph.
+// Context, workspace, host/device staging, error reporting, launch counting and
+// optional kernel timing of liblaph.
+#include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -8,6 +11,66 @@ namespace laph {
 static thread_local std::string g_last_error;
 
 void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+static std::atomic<long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct ProfEntry {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    long launches = 0;
+    double ms = 0.0, bytes = 0.0, flops = 0.0;
+};
+static std::mutex g_prof_mu;
+static bool g_prof = false;
+static std::map<std::string, ProfEntry> g_prof_tab;
+static std::vector<cudaEvent_t> g_event_pool;
+static thread_local cudaEvent_t g_open_start = nullptr;
+
+static cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    LAPH_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+bool prof_on() { return g_prof; }
+
+void prof_begin(const char *, cudaStream_t s) {
+    if (!g_prof) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_open_start = take_event();
+    LAPH_CUDA(cudaEventRecord(g_open_start, s));
+}
+
+static void drain(ProfEntry &e) {
+    for (auto &p : e.pending) {
+        LAPH_CUDA(cudaEventSynchronize(p.second));
+        float ms = 0.f;
+        LAPH_CUDA(cudaEventElapsedTime(&ms, p.first, p.second));
+        e.ms += ms;
+        g_event_pool.push_back(p.first);
+        g_event_pool.push_back(p.second);
+    }
+    e.pending.clear();
+}
+
+void prof_end(const char *family, cudaStream_t s, double bytes, double flops) {
+    if (!g_prof || !g_open_start) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t stop = take_event();
+    LAPH_CUDA(cudaEventRecord(stop, s));
+    ProfEntry &e = g_prof_tab[family];
+    e.pending.emplace_back(g_open_start, stop);
+    g_open_start = nullptr;
+    e.launches += 1;
+    e.bytes += bytes;
+    e.flops += flops;
+    if (e.pending.size() > 4096) drain(e);
+}
 
 void ctx_activate(laph_ctx *ctx) {
     LAPH_REQUIRE(ctx != nullptr, "context is null");
@@ -120,3 +183,38 @@ extern "C" void laph_ctx_destroy(laph_ctx *ctx) {
 extern "C" const char *laph_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char *laph_version(void) { return "laph-gb300 0.1 (sm_103a)"; }
+
+extern "C" long laph_launch_count(void) { return g_launches.load(); }
+
+extern "C" void laph_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof = on != 0;
+}
+
+extern "C" void laph_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &kv : g_prof_tab) {
+        try {
+            drain(kv.second);
+        } catch (...) {
+        }
+    }
+    g_prof_tab.clear();
+}
+
+extern "C" int laph_profile_read(const char *family, long *launches, double *ms, double *bytes, double *flops) {
+    return guard([&] {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        auto it = g_prof_tab.find(family ? family : "");
+        if (it == g_prof_tab.end()) {
+            *launches = 0;
+            *ms = *bytes = *flops = 0.0;
+            return;
+        }
+        drain(it->second);
+        *launches = it->second.launches;
+        *ms = it->second.ms;
+        *bytes = it->second.bytes;
+        *flops = it->second.flops;
+    });
+}

@@ -229,12 +229,30 @@ __global__ void __launch_bounds__(256) hop_kernel(DiracOp op, int p, cpx<T> *__r
     for (int k = 0; k < 12; ++k) dst[(long)k * nr] = res[k];
 }
 
+// Algorithmic traffic of one hop launch over the Vh output sites of a parity:
+// each neighbour spinor is read once per launch (24 reals), the output written
+// once (24 reals), the xpay/residual operands read once (24 reals each); the 8
+// links touching a site are read once per launch (12 reals compressed for FP32,
+// 18 for FP64) and the clover block once (72 reals).
+double hop_bytes(const DiracOp &op, HopMode mode, int nr, size_t real_bytes) {
+    double spin = 24.0 * real_bytes;
+    double per_rhs = 2.0 * spin + (mode == HOP_CLOVINV ? 0.0 : spin) + (mode == HOP_RESID || mode == HOP_APPLY ? spin : 0.0);
+    double link_reals = real_bytes == 4 ? 12.0 : 18.0;
+    double per_site = 8.0 * link_reals * real_bytes + 72.0 * (mode == HOP_CLOVINV || mode == HOP_CLOVINV_XPAY ? real_bytes : 8.0);
+    return (double)op.g.Vh * (nr * per_rhs + per_site);
+}
+
+// Conventional flop count per output site and right-hand side: 1320 (Wilson
+// hopping term) + 504 (two 6x6 complex clover blocks).
+double hop_flops(const DiracOp &op, int nr) { return (double)op.g.Vh * nr * 1824.0; }
+
 template <typename T>
 void hop(const DiracOp &op, int p, HopMode mode, cpx<T> *out, const cpx<T> *in, const cpx<T> *z, const cpx<T> *xp,
          int nr, cudaStream_t s) {
     long n = op.g.Vh * nr;
     const int block = 128;
     unsigned grid = grid_for(n, block);
+    prof_begin("dslash_fp64", s);
     switch (mode) {
         case HOP_CLOVINV: hop_kernel<T, HOP_CLOVINV><<<grid, block, 0, s>>>(op, p, out, in, z, xp, nr); break;
         case HOP_CLOVINV_XPAY: hop_kernel<T, HOP_CLOVINV_XPAY><<<grid, block, 0, s>>>(op, p, out, in, z, xp, nr); break;
@@ -242,6 +260,7 @@ void hop(const DiracOp &op, int p, HopMode mode, cpx<T> *out, const cpx<T> *in, 
         case HOP_RESID: hop_kernel<T, HOP_RESID><<<grid, block, 0, s>>>(op, p, out, in, z, xp, nr); break;
     }
     LAPH_LAUNCH_CHECK();
+    prof_end("dslash_fp64", s, hop_bytes(op, mode, nr, sizeof(T)), hop_flops(op, nr));
 }
 
 template void hop<double>(const DiracOp &, int, HopMode, c64 *, const c64 *, const c64 *, const c64 *, int, cudaStream_t);
@@ -252,11 +271,13 @@ void hop<float>(const DiracOp &op, int p, HopMode mode, c32 *out, const c32 *in,
     long n = op.g.Vh * nr;
     const int block = 128;
     unsigned grid = grid_for(n, block);
+    prof_begin("dslash_fp32", s);
     if (mode == HOP_CLOVINV)
         hop_kernel<float, HOP_CLOVINV><<<grid, block, 0, s>>>(op, p, out, in, z, xp, nr);
     else
         hop_kernel<float, HOP_CLOVINV_XPAY><<<grid, block, 0, s>>>(op, p, out, in, z, xp, nr);
     LAPH_LAUNCH_CHECK();
+    prof_end("dslash_fp32", s, hop_bytes(op, mode, nr, sizeof(float)), hop_flops(op, nr));
 }
 
 // ------------------------------------------------------------ clover inverse only

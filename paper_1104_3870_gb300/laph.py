@@ -91,6 +91,11 @@ _sig = {
                                         ctypes.c_int, _vp]),
     "laph_sinks": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "correlate": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
+    "laph_launch_count": (ctypes.c_long, []),
+    "laph_profile_enable": (None, [ctypes.c_int]),
+    "laph_profile_reset": (None, []),
+    "laph_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
 for _name, (_res, _args) in _sig.items():
     if hasattr(_lib, _name):
@@ -164,6 +169,26 @@ class Context:
 
 def version():
     return _lib.laph_version().decode()
+
+
+def laph_launch_count():
+    return int(_lib.laph_launch_count())
+
+
+def laph_profile_enable(on=True):
+    _lib.laph_profile_enable(int(bool(on)))
+
+
+def laph_profile_reset():
+    _lib.laph_profile_reset()
+
+
+def laph_profile_read(family):
+    """(launches, total ms, algorithmic bytes, flops) of a kernel family timed with CUDA events."""
+    n = ctypes.c_long()
+    ms, b, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.laph_profile_read(family.encode(), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b), ctypes.byref(f)))
+    return n.value, ms.value, b.value, f.value
 
 
 def laph_stout_smear(ctx, lat, links, rho, nsteps, spatial_only, stream=None):
