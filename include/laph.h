@@ -271,6 +271,29 @@ typedef struct {
 int correlate(laph_ctx *ctx, const laph_lattice *lat, const laph_corr_spec *spec,
               const void *const *coef, const uint8_t *const *noise, void *corr, void *stream);
 
+/* ------------------------------------------------------------------------
+ * correlate_noalloc: the same correlators as correlate(), for callers that
+ * cannot allocate GPU memory (no counterpart in the paper; it exists for
+ * callers such as code running inside a caller-owned memory pool or arena,
+ * processes whose device memory is reserved up front, or loops that must not
+ * stall on an allocation).  It calls no cudaMalloc/cudaFree and no allocating
+ * library routine and needs no laph_ctx.
+ *   - coef[k], noise[k] and corr must be device pointers (LAPH_ERR_ARG
+ *     otherwise: host arrays would need staging memory); spec->b_list is a
+ *     host array.
+ *   - Scratch comes from one fixed 16 MiB __device__ array inside the
+ *     library, held by every GPU that loads it until the process exits.  A
+ *     problem needing more (about 2 nt nb^2 + 3 nt nb^2 for pi pi complex
+ *     doubles) is rejected with LAPH_ERR_ARG and a message giving the size.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents: calls
+ *     that overlap on the GPU (unordered streams or threads) race on it.
+ * ------------------------------------------------------------------------ */
+int correlate_noalloc(const laph_lattice *lat, const laph_corr_spec *spec, const void *const *coef,
+                      const uint8_t *const *noise, void *corr, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,7 @@ _sig = {
                                         ctypes.c_int, _vp]),
     "laph_sinks": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "correlate": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
+    "correlate_noalloc": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
     "laph_launch_count": (ctypes.c_long, []),
     "laph_profile_enable": (None, [ctypes.c_int]),
     "laph_profile_reset": (None, []),
@@ -242,3 +243,13 @@ def correlate(ctx, lat, channel, t0, nv, dil, b_list, coefs, noises, corr, strea
     cp = (_vp * len(coefs))(*[_ptr(c) for c in coefs])
     npt = (_vp * len(noises))(*[_ptr(n) for n in noises])
     _check(_lib.correlate(ctx.ptr, ctypes.byref(lat), ctypes.byref(spec), cp, npt, _ptr(corr), _stream(stream)))
+
+
+def correlate_noalloc(lat, channel, t0, nv, dil, b_list, coefs, noises, corr, stream=None):
+    """correlate() without any GPU allocation: device arrays only, scratch in the
+    library's fixed device array (see include/laph.h)."""
+    b = np.ascontiguousarray(np.asarray(b_list, dtype=np.int32))
+    spec = CorrSpec(int(channel), int(t0), int(nv), dil, len(b), b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    cp = (_vp * len(coefs))(*[_ptr(c) for c in coefs])
+    npt = (_vp * len(noises))(*[_ptr(n) for n in noises])
+    _check(_lib.correlate_noalloc(ctypes.byref(lat), ctypes.byref(spec), cp, npt, _ptr(corr), _stream(stream)))
