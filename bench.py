@@ -42,6 +42,7 @@ def parse_args(argv=None):
     p.add_argument("--mode", choices=["mixed", "plain"], default="mixed")
     p.add_argument("--plain-sample", type=int, default=2, help="sources solved by the plain FP64 comparison")
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per solver launch (0: all)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args(argv)
 
@@ -155,6 +156,60 @@ def oracle_sample(wl, seconds=15.0, threads=None):
                       f"at this m0; eigenvectors, sources, sinks and contractions not included"}
 
 
+# ----------------------------------------------------------------------------- ncu traffic record
+HOP_KERNEL_VERSION = "hop_v1"
+
+
+def measured_traffic_ratio(workload):
+    """DRAM bytes over algorithmic bytes of one captured hop_kernel<float> launch, from the
+    committed ncu summary (profiles/hop_kernel_fp32_<workload>.md, line
+    'traffic_bytes_per_launch: N version V nr R algorithmic A'); None when absent or taken on
+    another kernel version.  The capture uses a smaller RHS block than the bench (device
+    memory rule for ncu); traffic scales with the sites x RHS processed, so the bench
+    reports ratio x its own algorithmic bytes per launch."""
+    path = os.path.join(ROOT, "profiles", f"hop_kernel_fp32_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 8 and parts[0] == "traffic_bytes_per_launch:" and parts[2] == "version":
+            if parts[3] == HOP_KERNEL_VERSION and parts[6] == "algorithmic":
+                return float(parts[1]) / float(parts[7])
+    return None
+
+
+def profiled_step(L, path, torch, stream, u, ut, evals, evecs, rhs, sol, coef, codes, corr, channels, nnoise, nb,
+                  noise_ids, wl, bs, t0, mode, rhs_block):
+    """ms per stage (CUDA events on the launching stream) and per kernel family of one step."""
+    torch.cuda.synchronize()
+    L.laph_profile_reset()
+    L.laph_profile_enable(2)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev[0].record(stream)
+    path.eigvecs(ut, evals, evecs)
+    ev[1].record(stream)
+    for k in range(nnoise):
+        path.sources(evecs, noise_ids[k], wl.config_id, bs, out=rhs[k * nb:(k + 1) * nb], codes=codes[k])
+    ev[2].record(stream)
+    path.solve(u, rhs, mode=mode, sol=sol, rhs_block=rhs_block)
+    ev[3].record(stream)
+    path.sinks(evecs, sol, out=coef)
+    ev[4].record(stream)
+    for i, ch in enumerate(channels):
+        path.correlate(ch, t0, bs, [coef[0:nb], coef[nb:2 * nb]], [codes[0], codes[1]], out=corr[i])
+    ev[5].record(stream)
+    torch.cuda.synchronize()
+    L.laph_profile_enable(0)
+    names = ["eigvecs", "sources", "solve", "sinks", "correlate"]
+    stages = {n: ev[i].elapsed_time(ev[i + 1]) for i, n in enumerate(names)}
+    fams = {}
+    for f in L.laph_profile_families():
+        n, ms, by, fl = L.laph_profile_read(f)
+        fams[f] = {"launches": n, "ms": ms}
+    L.laph_profile_reset()
+    return {"stage_ms": stages, "family_ms": fams}
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -195,7 +250,7 @@ def run_ours(args):
         _, _, rep = path.eigvecs(ut_in, evals, evecs)
         for k in range(nnoise):
             path.sources(evecs, noise_ids[k], wl.config_id, bs, out=rhs[k * nb:(k + 1) * nb], codes=codes[k])
-        _, reps = path.solve(u_in, rhs, mode=mode, sol=sol)
+        _, reps = path.solve(u_in, rhs, mode=mode, sol=sol, rhs_block=args.rhs_block)
         path.sinks(evecs, sol, out=coef)
         for i, ch in enumerate(channels):
             path.correlate(ch, t0, bs, [coef[0:nb], coef[nb:2 * nb]], [codes[0], codes[1]], out=corr[i])
@@ -211,7 +266,7 @@ def run_ours(args):
     barrier(world)
     clocks = ClockSampler(local) if rank == 0 else None
     L.laph_profile_reset()
-    L.laph_profile_enable(True)
+    L.laph_profile_enable(1)
     launches0 = L.laph_launch_count()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -222,7 +277,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = L.laph_launch_count() - launches0
-    L.laph_profile_enable(False)
+    L.laph_profile_enable(0)
     clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = aggregate_max(ms, world, device="cuda")
@@ -238,17 +293,17 @@ def run_ours(args):
     else:
         fam, n, kms, kbytes = "dslash_fp64 (hop_kernel<double>)", n64, ms64, by64
     achieved = kbytes / (kms / 1000.0) / 1e9 if kms else None
-    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
-    traffic = None
-    if os.path.exists(traffic_file):
-        tr = json.load(open(traffic_file))
-        if tr.get("kernel_version") == "hop_v1" and tr.get("workload") == wl.name:
-            traffic = tr.get("bytes_per_launch")
+    ratio = measured_traffic_ratio(wl.name)
+    traffic = ratio * kbytes / n if (ratio and n and mode == L.MIXED_FP32) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
                 "kernel": fam, "launches": n, "avg_launch_us": 1000.0 * kms / n if n else None,
                 "algorithmic_bytes_per_launch": kbytes / n if n else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+
+    # one more (untimed) step with every kernel family timed and per-stage events: the breakdown
+    breakdown = profiled_step(L, path, torch, stream, u, ut, evals, evecs, rhs, sol, coef, codes, corr, channels,
+                              nnoise, nb, noise_ids, wl, bs, t0, mode, args.rhs_block)
 
     # e2e through the public API with host buffers: links in pinned host memory are staged by the
     # library each call; the correlators are read back to host.
@@ -259,7 +314,7 @@ def run_ours(args):
     for _ in range(args.e2e_steps):
         step(u_h, ut_h, read_back=True)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t) / args.e2e_steps
+    e2e_s = (time.perf_counter() - t) / max(args.e2e_steps, 1)
     e2e_s = aggregate_max(e2e_s, world, device="cuda")
     e2e = {"value": whole_job_rate(nsrc, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(u_h.numel() * u_h.element_size() * 2),
@@ -298,7 +353,7 @@ def run_ours(args):
                                    f"at t0={t0}, {nnoise} noises x {nb} projectors per replica",
                        "sources_per_step": nsrc, "solver": args.mode, "tol": 1e-10,
                        "l2": "inputs larger than L2 (solver working set > 1 GB)", "parallelism": f"replicas{world}"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "breakdown": breakdown,
             "variants": variants,
             "path_stats": {"true_resid_max": stats.get("resid"), "inner_iters_max": max(stats.get("iters", [0])),
                            "eig_restarts_matvecs_resid": stats.get("eig")}}

@@ -76,6 +76,21 @@ const char *laph_last_error(void);
 /* Library version string. */
 const char *laph_version(void);
 
+/* Measurement helpers (not part of the paper's method).
+ * laph_launch_count: number of kernels the library has launched so far.
+ * laph_profile_enable(level): 0 off; 1 time every Dirac-stencil launch with
+ *   CUDA events on its stream; 2 time every instrumented kernel family.
+ * laph_profile_read: launches, total milliseconds, algorithmic bytes and
+ *   flops accumulated for one family (e.g. "dslash_fp32"); synchronises on
+ *   the recorded events.  laph_profile_families writes the comma-separated
+ *   family names into buf (returns the full length).  laph_profile_reset
+ *   clears the table. */
+long laph_launch_count(void);
+void laph_profile_enable(int level);
+void laph_profile_reset(void);
+int laph_profile_families(char *buf, int len);
+int laph_profile_read(const char *family, long *launches, double *ms, double *bytes, double *flops);
+
 /* ------------------------------------------------------------------------
  * Gauge preparation: stout smearing (Sec. II: spatial links smeared with
  * the stout recipe, only spatial staples, temporal links not smeared).

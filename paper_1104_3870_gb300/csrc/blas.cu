@@ -19,18 +19,22 @@ RedPlan red_plan(laph_ctx *ctx, long nrows, int nr) {
 }
 
 // ------------------------------------------------------------------ reductions
+// Each thread accumulates its rows in the precision of the data (Body::Acc: FP32 for the
+// inner solver, FP64 for the outer one; FP64 arithmetic is scarce on this GPU), then the
+// block tree and the cross-block sum run in FP64.
 template <int NRED, class Body>
 __global__ void red_kernel(long nrows, int nr, int rpb, Body body, c64 *partial) {
+    using Acc = typename Body::Acc;
     extern __shared__ c64 sm[];
     const int tid = threadIdx.x, bd = blockDim.x;
     const int r = tid % nr, row0 = tid / nr;
-    c64 acc[NRED];
+    Acc acc[NRED];
 #pragma unroll
-    for (int k = 0; k < NRED; ++k) acc[k] = {0.0, 0.0};
+    for (int k = 0; k < NRED; ++k) acc[k] = {0, 0};
     for (long row = (long)blockIdx.x * rpb + row0; row < nrows; row += (long)gridDim.x * rpb)
         body(row * nr + r, r, acc);
 #pragma unroll
-    for (int k = 0; k < NRED; ++k) sm[k * bd + tid] = acc[k];
+    for (int k = 0; k < NRED; ++k) sm[k * bd + tid] = cvt<double>(acc[k]);
     __syncthreads();
     for (int st = rpb / 2; st > 0; st >>= 1) {
         if (row0 < st)
@@ -63,32 +67,38 @@ template <int NRED, class Body>
 static void run_reduce(laph_ctx *ctx, const RedPlan &pl, long nrows, const Body &body, c64 *out, cudaStream_t s) {
     c64 *partial = (c64 *)ws_get(ctx, "red:partial", sizeof(c64) * pl.grid * NRED * pl.nr);
     size_t shm = sizeof(c64) * NRED * pl.block;
+    const char *fam = sizeof(typename Body::Acc) == 8 ? "blas_fp32" : "blas_fp64";
+    prof_begin(fam, s);
     red_kernel<NRED, Body><<<pl.grid, pl.block, shm, s>>>(nrows, pl.nr, pl.rpb, body, partial);
     LAPH_LAUNCH_CHECK();
     red_final<<<NRED * pl.nr, 256, 0, s>>>(partial, (int)pl.grid, NRED, pl.nr, out);
     LAPH_LAUNCH_CHECK();
+    prof_end(fam, s, 0.0, 0.0);
 }
 
 template <typename T>
 struct Dots1 {
+    using Acc = cpx<T>;
     const cpx<T> *a0, *b0;
-    __device__ void operator()(long i, int, c64 *acc) const { acc[0] += cmul_conj(cvt<double>(a0[i]), cvt<double>(b0[i])); }
+    __device__ void operator()(long i, int, Acc *acc) const { acc[0] += cmul_conj(a0[i], b0[i]); }
 };
 template <typename T>
 struct Dots2 {
+    using Acc = cpx<T>;
     const cpx<T> *a0, *b0, *a1, *b1;
-    __device__ void operator()(long i, int, c64 *acc) const {
-        acc[0] += cmul_conj(cvt<double>(a0[i]), cvt<double>(b0[i]));
-        acc[1] += cmul_conj(cvt<double>(a1[i]), cvt<double>(b1[i]));
+    __device__ void operator()(long i, int, Acc *acc) const {
+        acc[0] += cmul_conj(a0[i], b0[i]);
+        acc[1] += cmul_conj(a1[i], b1[i]);
     }
 };
 template <typename T>
 struct Dots3 {
+    using Acc = cpx<T>;
     const cpx<T> *a0, *b0, *a1, *b1, *a2, *b2;
-    __device__ void operator()(long i, int, c64 *acc) const {
-        acc[0] += cmul_conj(cvt<double>(a0[i]), cvt<double>(b0[i]));
-        acc[1] += cmul_conj(cvt<double>(a1[i]), cvt<double>(b1[i]));
-        acc[2] += cmul_conj(cvt<double>(a2[i]), cvt<double>(b2[i]));
+    __device__ void operator()(long i, int, Acc *acc) const {
+        acc[0] += cmul_conj(a0[i], b0[i]);
+        acc[1] += cmul_conj(a1[i], b1[i]);
+        acc[2] += cmul_conj(a2[i], b2[i]);
     }
 };
 
@@ -120,8 +130,10 @@ __global__ void axpy_scaled_kernel(long n, int nr, const double *scale, const cp
 template <typename Tx, typename Ty>
 void mrhs_axpy_scaled(long nrows, int nr, const double *scale, const cpx<Tx> *x, cpx<Ty> *y, cudaStream_t s) {
     long n = nrows * nr;
+    prof_begin("blas_convert", s);
     axpy_scaled_kernel<Tx, Ty><<<grid_for(n, 256), 256, 0, s>>>(n, nr, scale, x, y);
     LAPH_LAUNCH_CHECK();
+    prof_end("blas_convert", s, 0.0, 0.0);
 }
 template void mrhs_axpy_scaled<float, double>(long, int, const double *, const c32 *, c64 *, cudaStream_t);
 template void mrhs_axpy_scaled<double, double>(long, int, const double *, const c64 *, c64 *, cudaStream_t);
@@ -137,8 +149,10 @@ __global__ void copy_scaled_kernel(long n, int nr, const double *scale, const cp
 template <typename Tx, typename Ty>
 void mrhs_copy_scaled(long nrows, int nr, const double *scale, const cpx<Tx> *x, cpx<Ty> *y, cudaStream_t s) {
     long n = nrows * nr;
+    prof_begin("blas_convert", s);
     copy_scaled_kernel<Tx, Ty><<<grid_for(n, 256), 256, 0, s>>>(n, nr, scale, x, y);
     LAPH_LAUNCH_CHECK();
+    prof_end("blas_convert", s, 0.0, 0.0);
 }
 template void mrhs_copy_scaled<double, float>(long, int, const double *, const c64 *, c32 *, cudaStream_t);
 template void mrhs_copy_scaled<double, double>(long, int, const double *, const c64 *, c64 *, cudaStream_t);
@@ -166,8 +180,11 @@ template <typename T>
 void bicg_p_update(long nrows, int nr, const BicgScalars &sc, const cpx<T> *r, cpx<T> *p, const cpx<T> *v,
                    cudaStream_t s) {
     long n = nrows * nr;
+    const char *fam = sizeof(T) == 4 ? "blas_fp32" : "blas_fp64";
+    prof_begin(fam, s);
     p_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(n, nr, sc, r, p, v);
     LAPH_LAUNCH_CHECK();
+    prof_end(fam, s, 0.0, 0.0);
 }
 
 template <typename T>
@@ -181,8 +198,11 @@ template <typename T>
 void bicg_s_update(long nrows, int nr, const BicgScalars &sc, const cpx<T> *r, const cpx<T> *v, cpx<T> *sv,
                    cudaStream_t s) {
     long n = nrows * nr;
+    const char *fam = sizeof(T) == 4 ? "blas_fp32" : "blas_fp64";
+    prof_begin(fam, s);
     s_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(n, nr, sc, r, v, sv);
     LAPH_LAUNCH_CHECK();
+    prof_end(fam, s, 0.0, 0.0);
 }
 
 template <typename T>
@@ -192,13 +212,14 @@ struct XRBody {
     const cpx<T> *p, *sv, *t;
     cpx<T> *r;
     const cpx<T> *rhat;
-    __device__ void operator()(long i, int k, c64 *acc) const {
+    using Acc = cpx<T>;
+    __device__ void operator()(long i, int k, Acc *acc) const {
         cpx<T> a = cvt<T>(sc.alpha[k]), w = cvt<T>(sc.omega[k]);
         x[i] = x[i] + a * p[i] + w * sv[i];
         cpx<T> rn = sv[i] - w * t[i];
         r[i] = rn;
-        acc[0] += cmul_conj(cvt<double>(rhat[i]), cvt<double>(rn));
-        acc[1] += cvt<double>(cmul_conj(rn, rn));
+        acc[0] += cmul_conj(rhat[i], rn);
+        acc[1] += cmul_conj(rn, rn);
     }
 };
 

@@ -21,7 +21,7 @@ struct ProfEntry {
     double ms = 0.0, bytes = 0.0, flops = 0.0;
 };
 static std::mutex g_prof_mu;
-static bool g_prof = false;
+static int g_prof = 0;   // 0 off, 1 stencil families only, 2 every instrumented family
 static std::map<std::string, ProfEntry> g_prof_tab;
 static std::vector<cudaEvent_t> g_event_pool;
 static thread_local cudaEvent_t g_open_start = nullptr;
@@ -37,10 +37,11 @@ static cudaEvent_t take_event() {
     return e;
 }
 
-bool prof_on() { return g_prof; }
+bool prof_on() { return g_prof != 0; }
 
-void prof_begin(const char *, cudaStream_t s) {
+void prof_begin(const char *family, cudaStream_t s) {
     if (!g_prof) return;
+    if (g_prof == 1 && std::strncmp(family, "dslash", 6) != 0) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_open_start = take_event();
     LAPH_CUDA(cudaEventRecord(g_open_start, s));
@@ -186,9 +187,9 @@ extern "C" const char *laph_version(void) { return "laph-gb300 0.1 (sm_103a)"; }
 
 extern "C" long laph_launch_count(void) { return g_launches.load(); }
 
-extern "C" void laph_profile_enable(int on) {
+extern "C" void laph_profile_enable(int level) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_prof = on != 0;
+    g_prof = level < 0 ? 0 : (level > 2 ? 2 : level);
 }
 
 extern "C" void laph_profile_reset(void) {
@@ -200,6 +201,17 @@ extern "C" void laph_profile_reset(void) {
         }
     }
     g_prof_tab.clear();
+}
+
+extern "C" int laph_profile_families(char *buf, int len) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::string all;
+    for (auto &kv : g_prof_tab) all += kv.first + ",";
+    if (buf && len > 0) {
+        std::strncpy(buf, all.c_str(), (size_t)len - 1);
+        buf[len - 1] = 0;
+    }
+    return (int)all.size();
 }
 
 extern "C" int laph_profile_read(const char *family, long *launches, double *ms, double *bytes, double *flops) {

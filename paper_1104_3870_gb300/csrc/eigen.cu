@@ -506,6 +506,7 @@ struct Lanczos {
         unsigned grid = grid_for(tot, 128);
         c64 *bufs[3] = {y, c0, c1};
         auto buf = [&](int k) { return bufs[(ncheb - k) % 3]; };
+        prof_begin("eig_cheb", s);
         cheb_kernel<<<grid, 128, 0, s>>>(g, U, 1, x, nullptr, buf(1), ca, cb, 1.0, 0, n, n);
         LAPH_LAUNCH_CHECK();
         for (int k = 2; k <= ncheb; ++k) {
@@ -513,6 +514,7 @@ struct Lanczos {
             cheb_kernel<<<grid, 128, 0, s>>>(g, U, 1, buf(k - 1), tm2, buf(k), ca, cb, 2.0, 1, n, n);
             LAPH_LAUNCH_CHECK();
         }
+        prof_end("eig_cheb", s, 0.0, 0.0);
         matvecs += ncheb;
     }
 
@@ -525,6 +527,7 @@ struct Lanczos {
         norm_only_kernel<<<nt, 256, 0, s>>>(n, w, nrm);
         LAPH_LAUNCH_CHECK();
         int cnt = j + 1;
+        prof_begin("eig_reorth", s);
         for (int pass = 0; pass <= 4; ++pass) {
             gemv_c_kernel<<<dim3(cnt, nt), 256, 0, s>>>(n, ldv, V, w, cnt, h, flag, pass);
             LAPH_LAUNCH_CHECK();
@@ -533,6 +536,7 @@ struct Lanczos {
             reorth_norm_kernel<<<nt, 256, 0, s>>>(n, ldv, w, h, H, j, cnt, nrm, flag, pass);
             LAPH_LAUNCH_CHECK();
         }
+        prof_end("eig_reorth", s, 0.0, 0.0);
         lanczos_next_kernel<<<dim3(grid_for(n, 256), nt), 256, 0, s>>>(n, ldv, j, w, nrm, V, H);
         LAPH_LAUNCH_CHECK();
     }
@@ -545,15 +549,19 @@ static void run_jacobi(int nt, int m, int ldh, const c64 *H, c64 *J, c64 *Yraw, 
     int npair = ((m + 1) & ~1) / 2;
     LAPH_REQUIRE(m <= 1024, "Krylov dimension above 1024 is not supported");
     size_t shm = sizeof(double) * 2 * 256 + sizeof(double) * 2 * npair + sizeof(c64) * npair + sizeof(int) * 2 * npair;
+    prof_begin("eig_jacobi", s);
     jacobi_kernel<<<nt, 256, shm, s>>>(m, ldh, H, J, Yraw, Y, theta, 60, ascending ? 1 : 0);
     LAPH_LAUNCH_CHECK();
+    prof_end("eig_jacobi", s, 0.0, 0.0);
 }
 
 // Out[t][c] = sum_j In[t][j] C[t][j][c]   (k x k coefficients, ldv input vectors per slice)
 static void rotate(long n, int nt, int ldv, int m, int k, const c64 *In, const c64 *C, c64 *Out, cudaStream_t s) {
     dim3 rg((unsigned)((n + 63) / 64), (unsigned)((k + 15) / 16), nt);
+    prof_begin("eig_gemm", s);
     rotate_kernel<<<rg, 256, 0, s>>>(n, ldv, m, k, In, C, Out);
     LAPH_LAUNCH_CHECK();
+    prof_end("eig_gemm", s, 0.0, 0.0);
 }
 
 }  // namespace laph

@@ -67,8 +67,10 @@ __global__ void __launch_bounds__(256) sinks_kernel(Geom g, int nv, int ncol, co
 void sinks(const Geom &g, int nv, int nrhs, const c64 *ev, const c64 *sol, c64 *coef, cudaStream_t s) {
     int ncol = 4 * nrhs;
     dim3 grid((nv + SK_TN - 1) / SK_TN, (ncol + SK_TC - 1) / SK_TC, g.nt);
+    prof_begin("sinks", s);
     sinks_kernel<<<grid, 256, 0, s>>>(g, nv, ncol, ev, sol, coef);
     LAPH_LAUNCH_CHECK();
+    prof_end("sinks", s, 0.0, 8.0 * nv * (double)ncol * 3.0 * g.V3 * g.nt);
 }
 
 }  // namespace laph

@@ -94,6 +94,7 @@ _sig = {
     "correlate_noalloc": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
     "laph_launch_count": (ctypes.c_long, []),
     "laph_profile_enable": (None, [ctypes.c_int]),
+    "laph_profile_families": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "laph_profile_reset": (None, []),
     "laph_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -176,8 +177,15 @@ def laph_launch_count():
     return int(_lib.laph_launch_count())
 
 
-def laph_profile_enable(on=True):
-    _lib.laph_profile_enable(int(bool(on)))
+def laph_profile_enable(level=1):
+    """0: off; 1: time the Dirac stencil launches; 2: time every instrumented kernel family."""
+    _lib.laph_profile_enable(int(level))
+
+
+def laph_profile_families():
+    buf = ctypes.create_string_buffer(4096)
+    _lib.laph_profile_families(buf, 4096)
+    return [f for f in buf.value.decode().split(",") if f]
 
 
 def laph_profile_reset():

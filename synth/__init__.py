@@ -121,7 +121,7 @@ WORKLOADS = {
                          dil_laph=(DIL_FULL, 0), source_times=tuple(range(8)), n_noise=2,
                          target_iters=150),
     # 16^3x32, N_v = 32, (TF, SF, LI8) fixed-time quark lines, 2 noises.
-    "medium_16x32": Workload("medium_16x32", ns=16, nt=32, xi=3.5, csw=1.0, m0=-0.1120, nv=32,
+    "medium_16x32": Workload("medium_16x32", ns=16, nt=32, xi=3.5, csw=1.0, m0=-0.0049, nv=32,
                              gauge_seed=1001, dil_time=(DIL_FULL, 0), dil_spin=(DIL_FULL, 0),
                              dil_laph=(DIL_INTERLACE, 8), source_times=(0,), n_noise=2,
                              target_iters=600),
