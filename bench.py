@@ -178,26 +178,69 @@ def measured_traffic_ratio(workload):
     return None
 
 
-def profiled_step(L, path, torch, stream, u, ut, evals, evecs, rhs, sol, coef, codes, corr, channels, nnoise, nb,
-                  noise_ids, wl, bs, t0, mode, rhs_block):
+class PathStep:
+    """Buffers and the five stages of one pass: eigenvectors, sources for every source
+    time and noise, one batched solve of all diluted sources, sinks, and the
+    correlators of every channel and source time."""
+
+    def __init__(self, L, torch, path, spec, wl, rank, mode, rhs_block, projectors_for_time):
+        self.L, self.torch, self.path, self.wl = L, torch, path, wl
+        self.mode, self.rhs_block = mode, rhs_block
+        self.t0s = list(wl.source_times)
+        self.bss = [projectors_for_time(spec, t0) for t0 in self.t0s]
+        self.nb = len(self.bss[0])
+        self.nnoise = wl.n_noise
+        self.nsrc = len(self.t0s) * self.nnoise * self.nb
+        self.noise_ids = [rank * self.nnoise + k for k in range(self.nnoise)]
+        self.rhs = path.field(self.nsrc)
+        self.sol = torch.empty_like(self.rhs)
+        self.coef = torch.empty((self.nsrc, wl.nt, 4, wl.nv), dtype=torch.complex128, device="cuda")
+        self.codes = torch.empty((self.nnoise, wl.nt, 4, wl.nv), dtype=torch.uint8, device="cuda")
+        self.evals = torch.empty((wl.nt, wl.nv), dtype=torch.float64, device="cuda")
+        self.evecs = torch.empty((wl.nt, wl.nv, wl.ns ** 3, 3), dtype=torch.complex128, device="cuda")
+        self.channels = [L.CH_PION, L.CH_SCALAR, L.CH_RHO]
+        self.corr = torch.empty((len(self.t0s), len(self.channels), wl.nt), dtype=torch.complex128, device="cuda")
+        self.corr_host = torch.empty_like(self.corr, device="cpu").pin_memory()
+        self.stats = {}
+
+    def block(self, ti, k):
+        o = (ti * self.nnoise + k) * self.nb
+        return slice(o, o + self.nb)
+
+    def run(self, u_in, ut_in, read_back=False, events=None):
+        p = self.path
+        mark = (lambda i: events[i].record(self.torch.cuda.current_stream())) if events else (lambda i: None)
+        mark(0)
+        _, _, rep = p.eigvecs(ut_in, self.evals, self.evecs)
+        mark(1)
+        for ti, bs in enumerate(self.bss):
+            for k in range(self.nnoise):
+                p.sources(self.evecs, self.noise_ids[k], self.wl.config_id, bs, out=self.rhs[self.block(ti, k)],
+                          codes=self.codes[k])
+        mark(2)
+        _, reps = p.solve(u_in, self.rhs, mode=self.mode, sol=self.sol, rhs_block=self.rhs_block)
+        mark(3)
+        p.sinks(self.evecs, self.sol, out=self.coef)
+        mark(4)
+        for ti, (t0, bs) in enumerate(zip(self.t0s, self.bss)):
+            for i, ch in enumerate(self.channels):
+                p.correlate(ch, t0, bs, [self.coef[self.block(ti, 0)], self.coef[self.block(ti, 1)]],
+                            [self.codes[0], self.codes[1]], out=self.corr[ti, i])
+        mark(5)
+        if read_back:
+            self.corr_host.copy_(self.corr, non_blocking=True)
+        self.stats["iters"] = [r.iters for r in reps]
+        self.stats["resid"] = max(r.true_resid for r in reps)
+        self.stats["eig"] = (rep.restarts, rep.matvecs, rep.max_resid)
+
+
+def profiled_step(L, torch, st, u, ut):
     """ms per stage (CUDA events on the launching stream) and per kernel family of one step."""
     torch.cuda.synchronize()
     L.laph_profile_reset()
     L.laph_profile_enable(2)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-    ev[0].record(stream)
-    path.eigvecs(ut, evals, evecs)
-    ev[1].record(stream)
-    for k in range(nnoise):
-        path.sources(evecs, noise_ids[k], wl.config_id, bs, out=rhs[k * nb:(k + 1) * nb], codes=codes[k])
-    ev[2].record(stream)
-    path.solve(u, rhs, mode=mode, sol=sol, rhs_block=rhs_block)
-    ev[3].record(stream)
-    path.sinks(evecs, sol, out=coef)
-    ev[4].record(stream)
-    for i, ch in enumerate(channels):
-        path.correlate(ch, t0, bs, [coef[0:nb], coef[nb:2 * nb]], [codes[0], codes[1]], out=corr[i])
-    ev[5].record(stream)
+    st.run(u, ut, events=ev)
     torch.cuda.synchronize()
     L.laph_profile_enable(0)
     names = ["eigvecs", "sources", "solve", "sinks", "correlate"]
@@ -229,36 +272,13 @@ def run_ours(args):
                        wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
     path = LapHPath(spec, local)
     u, ut = path.prepare_links(wl.gauge())          # a0: setup, not timed
-    t0 = wl.source_times[0]
-    bs = projectors_for_time(spec, t0)
-    nb, nnoise = len(bs), wl.n_noise
-    nsrc = nb * nnoise
-    noise_ids = [rank * nnoise + k for k in range(nnoise)]
     mode = L.MIXED_FP32 if args.mode == "mixed" else L.PLAIN_FP64
-    rhs = path.field(nsrc)
-    sol = torch.empty_like(rhs)
-    coef = torch.empty((nsrc, wl.nt, 4, wl.nv), dtype=torch.complex128, device="cuda")
-    codes = torch.empty((nnoise, wl.nt, 4, wl.nv), dtype=torch.uint8, device="cuda")
-    evals = torch.empty((wl.nt, wl.nv), dtype=torch.float64, device="cuda")
-    evecs = torch.empty((wl.nt, wl.nv, wl.ns ** 3, 3), dtype=torch.complex128, device="cuda")
-    channels = [L.CH_PION, L.CH_SCALAR, L.CH_RHO]
-    corr = torch.empty((len(channels), wl.nt), dtype=torch.complex128, device="cuda")
-    corr_host = torch.empty_like(corr, device="cpu").pin_memory()
-    stats = {}
+    st = PathStep(L, torch, path, spec, wl, rank, mode, args.rhs_block, projectors_for_time)
+    nsrc, nb, nnoise = st.nsrc, st.nb, st.nnoise
+    rhs, sol, corr_host, stats = st.rhs, st.sol, st.corr_host, st.stats
 
     def step(u_in, ut_in, read_back=False):
-        _, _, rep = path.eigvecs(ut_in, evals, evecs)
-        for k in range(nnoise):
-            path.sources(evecs, noise_ids[k], wl.config_id, bs, out=rhs[k * nb:(k + 1) * nb], codes=codes[k])
-        _, reps = path.solve(u_in, rhs, mode=mode, sol=sol, rhs_block=args.rhs_block)
-        path.sinks(evecs, sol, out=coef)
-        for i, ch in enumerate(channels):
-            path.correlate(ch, t0, bs, [coef[0:nb], coef[nb:2 * nb]], [codes[0], codes[1]], out=corr[i])
-        if read_back:
-            corr_host.copy_(corr, non_blocking=True)
-        stats["iters"] = [r.iters for r in reps]
-        stats["resid"] = max(r.true_resid for r in reps)
-        stats["eig"] = (rep.restarts, rep.matvecs, rep.max_resid)
+        st.run(u_in, ut_in, read_back=read_back)
 
     for _ in range(args.warmup):
         step(u, ut)
@@ -302,8 +322,7 @@ def run_ours(args):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
 
     # one more (untimed) step with every kernel family timed and per-stage events: the breakdown
-    breakdown = profiled_step(L, path, torch, stream, u, ut, evals, evecs, rhs, sol, coef, codes, corr, channels,
-                              nnoise, nb, noise_ids, wl, bs, t0, mode, args.rhs_block)
+    breakdown = profiled_step(L, torch, st, u, ut)
 
     # e2e through the public API with host buffers: links in pinned host memory are staged by the
     # library each call; the correlators are read back to host.
@@ -349,8 +368,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32/f64" if mode == L.MIXED_FP32 else "f64", "data": "synthetic",
-            "config": {"workload": f"{wl.name}: {wl.ns}^3x{wl.nt}, xi={wl.xi}, N_v={wl.nv}, dilution (TF,SF,LI8) "
-                                   f"at t0={t0}, {nnoise} noises x {nb} projectors per replica",
+            "config": {"workload": f"{wl.name}: {wl.ns}^3x{wl.nt}, xi={wl.xi}, N_v={wl.nv}, dilution "
+                                   f"{(wl.dil_time, wl.dil_spin, wl.dil_laph)} at source times {list(wl.source_times)}, "
+                                   f"{nnoise} noises x {nb} projectors each per replica",
                        "sources_per_step": nsrc, "solver": args.mode, "tol": 1e-10,
                        "l2": "inputs larger than L2 (solver working set > 1 GB)", "parallelism": f"replicas{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "breakdown": breakdown,

@@ -239,6 +239,39 @@ int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const void *links,
                       const laph_dirac_params *dirac, const void *rhs, void *sol, int nrhs,
                       const laph_solver_params *params, laph_solve_report *report, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned preconditioner for LAPH_SOLVE_LEARNED (the paper has no learned
+ * component; the network is this library's addition).  A linear,
+ * gauge-covariant network of 4 layers with 1 -> 4 -> 4 -> 4 -> 1 complex
+ * channels:
+ *   out_c(x) = sum_{c'} sum_{d=0..8} W[d][c][c'] (T_d in_{c'})(x),
+ *   T_0 = 1, T_{1+mu} psi(x) = s U_mu(x) psi(x+mu), T_{5+mu} psi(x) = s U_mu(x-mu)^dag psi(x-mu),
+ * s = -1 for hops across the time boundary; W[d][c][c'] is a 4x4 complex
+ * spin matrix acting as the identity on colour (so N(G psi; U^G) = G N(psi; U)).
+ * Weights: float array of laph_precond_size() entries, layers in order, each
+ * [9][c_out][c_in][4][4] complex as (re, im).  Training minimises
+ * (1/B) sum_i ||N(rho_i) - phi_i||^2 / ||phi_i||^2 over pairs with K phi_i = rho_i
+ * (Adam on the real and imaginary parts, FP32 network, FP64 gradient sums).
+ * All arrays may be host or device memory; rho/phi are [npairs][V][4][3] c128.
+ * ------------------------------------------------------------------------ */
+int laph_precond_size(void);
+/* Seeded start: channel 0 carries the identity (1/diag in the last layer), other weights small. */
+int laph_precond_init(uint64_t seed, double diag, float *weights);
+/* epochs over the pairs in batches of `batch`; weights and adam ([2][size] floats,
+ * first then second moments, zero at the start) are updated in place; step0 counts
+ * the Adam steps already taken; loss (optional) receives the mean batch loss. */
+int laph_precond_train(laph_ctx *ctx, const laph_lattice *lat, const void *links, const laph_dirac_params *dirac,
+                       const void *rho, const void *phi, int npairs, int epochs, int batch, double lr, int step0,
+                       float *weights, float *adam, double *loss, void *stream);
+/* Loss over all pairs (one batch, npairs <= 256) and its gradient dL/d conj(W) as c128
+ * in the weight layout. */
+int laph_precond_grad(laph_ctx *ctx, const laph_lattice *lat, const void *links, const laph_dirac_params *dirac,
+                      const float *weights, const void *rho, const void *phi, int npairs, double *loss, void *grad,
+                      void *stream);
+/* out = N(in) for nrhs fields (c128). */
+int laph_precond_apply(laph_ctx *ctx, const laph_lattice *lat, const void *links, const laph_dirac_params *dirac,
+                       const float *weights, const void *in, void *out, int nrhs, void *stream);
+
 /* Applies K (FP64) to nrhs fields: out = K in (layouts as dirac_solve_batch). */
 int laph_dirac_apply(laph_ctx *ctx, const laph_lattice *lat, const void *links,
                      const laph_dirac_params *dirac, const void *in, void *out, int nrhs,

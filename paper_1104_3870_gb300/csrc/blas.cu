@@ -155,6 +155,8 @@ void mrhs_copy_scaled(long nrows, int nr, const double *scale, const cpx<Tx> *x,
     prof_end("blas_convert", s, 0.0, 0.0);
 }
 template void mrhs_copy_scaled<double, float>(long, int, const double *, const c64 *, c32 *, cudaStream_t);
+template void mrhs_copy_scaled<float, double>(long, int, const double *, const c32 *, c64 *, cudaStream_t);
+template void mrhs_copy_scaled<float, float>(long, int, const double *, const c32 *, c32 *, cudaStream_t);
 template void mrhs_copy_scaled<double, double>(long, int, const double *, const c64 *, c64 *, cudaStream_t);
 
 __global__ void sub_kernel(long n, const c64 *x, const c64 *y, c64 *z) {

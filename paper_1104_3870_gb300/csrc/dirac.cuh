@@ -30,7 +30,15 @@ struct DiracOp {
     double *cinv64 = nullptr;  // A^{-1}  [2][Vh][2][36]
     float *cinv32 = nullptr;   // A^{-1}  [2][Vh][2][36]
     __nv_bfloat16 *cinv16 = nullptr;  // A^{-1} [2][Vh][2][36]
+    // FP32 inner-operator operands in packed form (dslash_f32.cu)
+    int *nbr = nullptr;       // [2][Vh][8] neighbour table, sign-folded
+    float4 *L32w = nullptr;   // [2][4][Vh][9] (re, re, im, im)
+    float *C32w = nullptr;    // [2][Vh][2][72] clover inverse
+    float *C32wA = nullptr;   // [2][Vh][2][72] clover A (full-lattice K for the learned solver)
 };
+
+// Builds nbr, L32w and C32w from L64 and cinv64 (called by prepare_dirac).
+void prepare_f32_operands(laph_ctx *ctx, DiracOp &op, cudaStream_t s);
 
 // Builds links/clover on the device from ABI links [V][4][3][3] c64 (device pointer).
 DiracOp prepare_dirac(laph_ctx *ctx, const Geom &g, const c64 *links, double m0, double csw, double xi,
@@ -49,6 +57,10 @@ enum HopMode {
 template <typename T>
 void hop(const DiracOp &op, int p, HopMode mode, cpx<T> *out, const cpx<T> *in, const cpx<T> *z,
          const cpx<T> *xp, int nr, cudaStream_t s);
+
+// FP32 hop with the packed operands of prepare_f32_operands (modes HOP_CLOVINV and HOP_CLOVINV_XPAY).
+void hop_f32(const DiracOp &op, int p, HopMode mode, cpx<float> *out, const cpx<float> *in, const cpx<float> *z,
+             int nr, cudaStream_t s);
 
 // BF16-stored inner operator: spinors, links and clover inverse in BF16, FP32 arithmetic.
 void hop_bf16(const DiracOp &op, int p, HopMode mode, __nv_bfloat162 *out, const __nv_bfloat162 *in,

@@ -267,17 +267,8 @@ template void hop<double>(const DiracOp &, int, HopMode, c64 *, const c64 *, con
 template <>
 void hop<float>(const DiracOp &op, int p, HopMode mode, c32 *out, const c32 *in, const c32 *z, const c32 *xp, int nr,
                 cudaStream_t s) {
-    LAPH_REQUIRE(mode == HOP_CLOVINV || mode == HOP_CLOVINV_XPAY, "FP32 hop supports the clover-inverse modes only");
-    long n = op.g.Vh * nr;
-    const int block = 128;
-    unsigned grid = grid_for(n, block);
-    prof_begin("dslash_fp32", s);
-    if (mode == HOP_CLOVINV)
-        hop_kernel<float, HOP_CLOVINV><<<grid, block, 0, s>>>(op, p, out, in, z, xp, nr);
-    else
-        hop_kernel<float, HOP_CLOVINV_XPAY><<<grid, block, 0, s>>>(op, p, out, in, z, xp, nr);
-    LAPH_LAUNCH_CHECK();
-    prof_end("dslash_fp32", s, hop_bytes(op, mode, nr, sizeof(float)), hop_flops(op, nr));
+    // packed-FP32 kernel of dslash_f32.cu; in apply mode the same-parity operand travels as z
+    hop_f32(op, p, mode, out, in, mode == HOP_APPLY ? xp : z, nr, s);
 }
 
 // ------------------------------------------------------------ clover inverse only

@@ -207,8 +207,8 @@ __global__ void scale_kernel(long n, c64 *v, const double *nrm) {
 // One block per slice: eigen-decomposition of the Hermitian m x m leading part of H
 // (row stride ldh).  Outputs theta[t][0..m) descending and Y[t][row][col] (eigenvectors in columns).
 __global__ void jacobi_kernel(int m, int ldh, const c64 *H, c64 *J, c64 *Y, c64 *Ysorted, double *theta,
-                              int max_sweeps, int ascending) {
-    extern __shared__ double jsm[];   // reduction scratch, then per-pair rotation parameters
+                              int max_sweeps, int ascending, int in_smem) {
+    extern __shared__ double jsm[];   // reduction scratch, per-pair rotation parameters, [A, Z]
     const int t = blockIdx.x;
     const int mm = (m + 1) & ~1;      // even count of players (a dummy index when m is odd)
     const int npair = mm / 2;
@@ -217,8 +217,10 @@ __global__ void jacobi_kernel(int m, int ldh, const c64 *H, c64 *J, c64 *Y, c64 
     c64 *ph = (c64 *)(sn + npair);
     int *pp = (int *)(ph + npair);
     int *qq = pp + npair;
-    c64 *A = J + (long)t * m * m;
-    c64 *Z = Y + (long)t * m * m;
+    // the working matrix and the rotations live in shared memory when they fit, else in global
+    c64 *sm_mats = (c64 *)(((uintptr_t)(qq + npair) + 15) & ~(uintptr_t)15);
+    c64 *A = in_smem ? sm_mats : J + (long)t * m * m;
+    c64 *Z = in_smem ? sm_mats + (long)m * m : Y + (long)t * m * m;
     const c64 *Hs = H + (long)t * ldh * ldh;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         int i = e / m, j = e % m;
@@ -549,8 +551,15 @@ static void run_jacobi(int nt, int m, int ldh, const c64 *H, c64 *J, c64 *Yraw, 
     int npair = ((m + 1) & ~1) / 2;
     LAPH_REQUIRE(m <= 1024, "Krylov dimension above 1024 is not supported");
     size_t shm = sizeof(double) * 2 * 256 + sizeof(double) * 2 * npair + sizeof(c64) * npair + sizeof(int) * 2 * npair;
+    size_t mats = 2 * sizeof(c64) * (size_t)m * m + 16;
+    const size_t smem_cap = 220 * 1024;   // below the 227 KB opt-in limit per block
+    int in_smem = (shm + mats <= smem_cap) ? 1 : 0;
+    if (in_smem) {
+        shm += mats;
+        LAPH_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    }
     prof_begin("eig_jacobi", s);
-    jacobi_kernel<<<nt, 256, shm, s>>>(m, ldh, H, J, Yraw, Y, theta, 60, ascending ? 1 : 0);
+    jacobi_kernel<<<nt, 256, shm, s>>>(m, ldh, H, J, Yraw, Y, theta, 60, ascending ? 1 : 0, in_smem);
     LAPH_LAUNCH_CHECK();
     prof_end("eig_jacobi", s, 0.0, 0.0);
 }
@@ -658,7 +667,7 @@ extern "C" int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *
         if (!(prm.lambda_C > 0)) {
             set_map({}, 1);
             start_vector();
-            int mest = m;
+            int mest = std::min(m, nv + 24);   // enough Ritz values to bound lambda_{nv+8} from above
             for (int j = 0; j < mest; ++j) lz.step(j);
             run_jacobi(nt, mest, m + 1, lz.H, J, Yraw, Y, theta, false, s);
             LAPH_CUDA(cudaMemcpyAsync(h_theta.data(), theta, sizeof(double) * nt * mest, cudaMemcpyDeviceToHost, s));
@@ -707,11 +716,12 @@ extern "C" int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *
                 break;
             }
             // The residual of a Ritz vector of T_n(B) has a floor of order eps ||T_n(B)||, which for a
-            // wide wanted spectrum lies above the tolerance on -Delta; once the restarts stop gaining
-            // (twice less than a factor 2), the kept block goes to the polish below.
+            // wide wanted spectrum lies above the tolerance on -Delta.  The kept block goes to the
+            // polish below once the restarts reach 1e-8 (the polish gains orders of magnitude per
+            // pass from there) or stop gaining (twice less than a factor 2).
             slow = (worst > 0.5 * prev_worst) ? slow + 1 : 0;
             prev_worst = std::min(prev_worst, worst);
-            if (restarts == max_restarts || (slow >= 2 && worst < 1e-4)) break;
+            if (restarts == max_restarts || worst < 1e-8 || (slow >= 2 && worst < 1e-4)) break;
             // thick restart: V[:, :keep] = Vt, V[:, keep] = V[:, m]; H = diag(theta) + coupling row
             copy_slices_kernel<<<dim3(grid_for(n, 256), nt), 256, 0, s>>>(n, lz.V + (long)m * n, (long)(m + 1) * n,
                                                                           lz.w, n);

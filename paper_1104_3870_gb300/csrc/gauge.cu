@@ -290,6 +290,7 @@ DiracOp prepare_dirac(laph_ctx *ctx, const Geom &g, const c64 *links, double m0,
     double diag = m0 + w[0] + w[1] + w[2] + w[3];
     clover_kernel<<<grid_for(g.V, 64), 64, 0, s>>>(g, links, diag, csw, op.clov64, op.cinv64, op.cinv32, op.cinv16);
     LAPH_LAUNCH_CHECK();
+    prepare_f32_operands(ctx, op, s);
     return op;
 }
 

@@ -13,6 +13,9 @@
 
 #include "blas.cuh"
 #include "dirac.cuh"
+#include "solver.cuh"
+
+extern "C" int laph_precond_size(void);
 
 namespace laph {
 
@@ -97,7 +100,7 @@ static InnerStats bicgstab_schur(laph_ctx *ctx, const DiracOp &op, int nr, const
 }
 
 // Solves one block of nr right-hand sides, columns [first, first+nr) of the ABI arrays.
-static void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int first, int nr,
+void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int first, int nr,
                         const laph_solver_params &prm, laph_solve_report *rep, cudaStream_t s) {
     const Geom &g = op.g;
     long nrows = g.Vh * 12;
@@ -130,28 +133,41 @@ static void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *s
     int total_iters = 0;
     const int max_outer = 100;
     for (int cyc = 0; cyc <= max_outer; ++cyc) {
-        // x_o = A_oo^{-1} b_o - A_oo^{-1} D_oe x_e, then the true residual r = b - K x
-        hop<double>(op, 1, HOP_CLOVINV_XPAY, xo, xe, to, nullptr, nr, s);
-        hop<double>(op, 0, HOP_RESID, re, xo, be, xe, nr, s);
-        hop<double>(op, 1, HOP_RESID, ro, xe, bo, xo, nr, s);
-        mrhs_dots<double>(ctx, pl, nrows, 2, re, re, ro, ro, nullptr, nullptr, red, s);
-        LAPH_CUDA(cudaMemcpyAsync(h_red.data(), red, sizeof(c64) * 2 * nr, cudaMemcpyDeviceToHost, s));
-        LAPH_CUDA(cudaStreamSynchronize(s));
         bool all = true;
         double worst = 0.0;
-        for (int k = 0; k < nr; ++k) {
-            double rn = std::sqrt(h_red[k].re + h_red[nr + k].re);
-            rel[k] = bnorm[k] > 0 ? rn / bnorm[k] : 0.0;
-            if (!(rel[k] <= tol)) {
-                all = false;
-                worst = std::max(worst, std::isfinite(rel[k]) ? rel[k] : 1e300);
+        if (cyc == 0) {
+            // x = 0: r = b, x_o = A_oo^{-1} b_o, and the Schur residual is bhat itself
+            LAPH_CUDA(cudaMemcpyAsync(xo, to, hb, cudaMemcpyDeviceToDevice, s));
+            LAPH_CUDA(cudaMemcpyAsync(re, bh, hb, cudaMemcpyDeviceToDevice, s));
+            for (int k = 0; k < nr; ++k) {
+                rel[k] = bnorm[k] > 0 ? 1.0 : 0.0;
+                if (rel[k] > tol) {
+                    all = false;
+                    worst = 1.0;
+                }
             }
+            if (all) break;
+        } else {
+            // x_o = A_oo^{-1} b_o - A_oo^{-1} D_oe x_e, then the true residual r = b - K x
+            hop<double>(op, 1, HOP_CLOVINV_XPAY, xo, xe, to, nullptr, nr, s);
+            hop<double>(op, 0, HOP_RESID, re, xo, be, xe, nr, s);
+            hop<double>(op, 1, HOP_RESID, ro, xe, bo, xo, nr, s);
+            mrhs_dots<double>(ctx, pl, nrows, 2, re, re, ro, ro, nullptr, nullptr, red, s);
+            LAPH_CUDA(cudaMemcpyAsync(h_red.data(), red, sizeof(c64) * 2 * nr, cudaMemcpyDeviceToHost, s));
+            LAPH_CUDA(cudaStreamSynchronize(s));
+            for (int k = 0; k < nr; ++k) {
+                double rn = std::sqrt(h_red[k].re + h_red[nr + k].re);
+                rel[k] = bnorm[k] > 0 ? rn / bnorm[k] : 0.0;
+                if (!(rel[k] <= tol)) {
+                    all = false;
+                    worst = std::max(worst, std::isfinite(rel[k]) ? rel[k] : 1e300);
+                }
+            }
+            if (all || cyc == max_outer || total_iters >= prm.maxiter) break;
+            // With x_o reconstructed from x_e the Schur residual bhat - M x_e equals A_ee^{-1} r_e.
+            clov_inv_apply<double>(op, 0, tmp, re, nr, s);
+            LAPH_CUDA(cudaMemcpyAsync(re, tmp, hb, cudaMemcpyDeviceToDevice, s));
         }
-        if (all || cyc == max_outer || total_iters >= prm.maxiter) break;
-        // Schur residual rhat = bhat - M x_e, normalised per RHS for the inner solve
-        hop<double>(op, 1, HOP_CLOVINV, tmp, xe, nullptr, nullptr, nr, s);
-        hop<double>(op, 0, HOP_CLOVINV_XPAY, re, tmp, xe, nullptr, nr, s);
-        mrhs_sub(nrows * nr, bh, re, re, s);
         mrhs_dots<double>(ctx, pl, nrows, 1, re, re, nullptr, nullptr, nullptr, nullptr, red, s);
         LAPH_CUDA(cudaMemcpyAsync(h_red.data(), red, sizeof(c64) * nr, cudaMemcpyDeviceToHost, s));
         LAPH_CUDA(cudaStreamSynchronize(s));
@@ -222,8 +238,10 @@ extern "C" int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const v
         if (prm.maxiter <= 0) prm.maxiter = 100000;
         if (!(prm.inner_tol > 0.0)) prm.inner_tol = 1e-5;
         if (prm.check_every <= 0) prm.check_every = 25;
-        LAPH_REQUIRE(prm.mode == LAPH_SOLVE_PLAIN_FP64 || prm.mode == LAPH_SOLVE_MIXED_FP32,
+        LAPH_REQUIRE(prm.mode == LAPH_SOLVE_PLAIN_FP64 || prm.mode == LAPH_SOLVE_MIXED_FP32 ||
+                         prm.mode == LAPH_SOLVE_LEARNED,
                      "solver mode not available in this build");
+        LAPH_REQUIRE(prm.mode != LAPH_SOLVE_LEARNED || prm.weights != nullptr, "learned mode needs weights");
         if (nrhs == 0) return;
         cudaStream_t s = as_stream(stream);
         size_t lbytes = sizeof(c64) * 36 * g.V;
@@ -232,13 +250,19 @@ extern "C" int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const v
         const c64 *b = (const c64 *)stage_in(ctx, rhs, fbytes, "rhs", s);
         StagedOut o = stage_out(ctx, sol, fbytes, "sol");
         DiracOp op = prepare_dirac(ctx, g, L, dirac->m0, dirac->csw, lat->xi, s);
+        const float *wdev = nullptr;
+        if (prm.mode == LAPH_SOLVE_LEARNED)
+            wdev = (const float *)stage_in(ctx, prm.weights, sizeof(float) * laph_precond_size(), "learned_w", s);
         int blk = prm.rhs_block;
         if (blk <= 0) blk = prm.mode == LAPH_SOLVE_PLAIN_FP64 ? 1 : std::min(nrhs, 64);
         blk = std::min(blk, std::min(nrhs, 256));
         std::vector<laph_solve_report> rep(nrhs);
         for (int first = 0; first < nrhs; first += blk) {
             int nr = std::min(blk, nrhs - first);
-            solve_block(ctx, op, b, (c64 *)o.dev, first, nr, prm, rep.data(), s);
+            if (prm.mode == LAPH_SOLVE_LEARNED)
+                solve_block_learned(ctx, op, wdev, b, (c64 *)o.dev, first, nr, prm, rep.data(), s);
+            else
+                solve_block(ctx, op, b, (c64 *)o.dev, first, nr, prm, rep.data(), s);
         }
         o.commit(s);
         LAPH_CUDA(cudaStreamSynchronize(s));

@@ -92,6 +92,15 @@ _sig = {
     "laph_sinks": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "correlate": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
     "correlate_noalloc": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
+    "laph_precond_size": (ctypes.c_int, []),
+    "laph_precond_init": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_double, _vp]),
+    "laph_precond_train": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), _vp, _vp,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _vp,
+                                          _vp, ctypes.POINTER(ctypes.c_double), _vp]),
+    "laph_precond_grad": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), _vp, _vp, _vp,
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
+    "laph_precond_apply": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), _vp, _vp, _vp,
+                                          ctypes.c_int, _vp]),
     "laph_launch_count": (ctypes.c_long, []),
     "laph_profile_enable": (None, [ctypes.c_int]),
     "laph_profile_families": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
@@ -251,6 +260,36 @@ def correlate(ctx, lat, channel, t0, nv, dil, b_list, coefs, noises, corr, strea
     cp = (_vp * len(coefs))(*[_ptr(c) for c in coefs])
     npt = (_vp * len(noises))(*[_ptr(n) for n in noises])
     _check(_lib.correlate(ctx.ptr, ctypes.byref(lat), ctypes.byref(spec), cp, npt, _ptr(corr), _stream(stream)))
+
+
+def laph_precond_size():
+    return int(_lib.laph_precond_size())
+
+
+def laph_precond_init(seed, diag, weights):
+    _check(_lib.laph_precond_init(int(seed), float(diag), _ptr(weights)))
+
+
+def laph_precond_train(ctx, lat, links, m0, csw, rho, phi, npairs, epochs, batch, lr, step0, weights, adam,
+                       stream=None):
+    loss = ctypes.c_double()
+    _check(_lib.laph_precond_train(ctx.ptr, ctypes.byref(lat), _ptr(links), ctypes.byref(DiracParams(m0, csw)),
+                                   _ptr(rho), _ptr(phi), int(npairs), int(epochs), int(batch), float(lr), int(step0),
+                                   _ptr(weights), _ptr(adam), ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def laph_precond_grad(ctx, lat, links, m0, csw, weights, rho, phi, npairs, grad, stream=None):
+    loss = ctypes.c_double()
+    _check(_lib.laph_precond_grad(ctx.ptr, ctypes.byref(lat), _ptr(links), ctypes.byref(DiracParams(m0, csw)),
+                                  _ptr(weights), _ptr(rho), _ptr(phi), int(npairs), ctypes.byref(loss), _ptr(grad),
+                                  _stream(stream)))
+    return loss.value
+
+
+def laph_precond_apply(ctx, lat, links, m0, csw, weights, inp, out, nrhs, stream=None):
+    _check(_lib.laph_precond_apply(ctx.ptr, ctypes.byref(lat), _ptr(links), ctypes.byref(DiracParams(m0, csw)),
+                                   _ptr(weights), _ptr(inp), _ptr(out), int(nrhs), _stream(stream)))
 
 
 def correlate_noalloc(lat, channel, t0, nv, dil, b_list, coefs, noises, corr, stream=None):

@@ -120,10 +120,11 @@ WORKLOADS = {
                          gauge_seed=1000, dil_time=(DIL_FULL, 0), dil_spin=(DIL_FULL, 0),
                          dil_laph=(DIL_FULL, 0), source_times=tuple(range(8)), n_noise=2,
                          target_iters=150),
-    # 16^3x32, N_v = 32, (TF, SF, LI8) fixed-time quark lines, 2 noises.
+    # 16^3x32, N_v = 32, (TF, SF, LI8) fixed-time quark lines at four widely separated
+    # source times (as in the paper's production runs), 2 noises: 256 diluted sources.
     "medium_16x32": Workload("medium_16x32", ns=16, nt=32, xi=3.5, csw=1.0, m0=-0.0049, nv=32,
                              gauge_seed=1001, dil_time=(DIL_FULL, 0), dil_spin=(DIL_FULL, 0),
-                             dil_laph=(DIL_INTERLACE, 8), source_times=(0,), n_noise=2,
+                             dil_laph=(DIL_INTERLACE, 8), source_times=(0, 8, 16, 24), n_noise=2,
                              target_iters=600),
     # 24^3x128, N_v = 64, (TI16, SF, LI8): 512 diluted sources per noise.
     "paper_24x128": Workload("paper_24x128", ns=24, nt=128, xi=3.5, csw=1.0, m0=-0.1120, nv=64,
