@@ -157,17 +157,17 @@ def oracle_sample(wl, seconds=15.0, threads=None):
 
 
 # ----------------------------------------------------------------------------- ncu traffic record
-HOP_KERNEL_VERSION = "hop_v1"
+HOP_KERNEL_VERSION = "hop3_tma_ns2"
 
 
 def measured_traffic_ratio(workload):
-    """DRAM bytes over algorithmic bytes of one captured hop_kernel<float> launch, from the
-    committed ncu summary (profiles/hop_kernel_fp32_<workload>.md, line
+    """DRAM bytes over algorithmic bytes of one captured FP32 hop launch (hop3_kernel), from the
+    committed ncu summary (profiles/hop3_kernel_fp32_<workload>.md, line
     'traffic_bytes_per_launch: N version V nr R algorithmic A'); None when absent or taken on
     another kernel version.  The capture uses a smaller RHS block than the bench (device
     memory rule for ncu); traffic scales with the sites x RHS processed, so the bench
     reports ratio x its own algorithmic bytes per launch."""
-    path = os.path.join(ROOT, "profiles", f"hop_kernel_fp32_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"hop3_kernel_fp32_{workload}.md")
     if not os.path.exists(path):
         return None
     for line in open(path):
@@ -309,7 +309,7 @@ def run_ours(args):
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     if mode == L.MIXED_FP32 and n32:
-        fam, n, kms, kbytes = "dslash_fp32 (hop_kernel<float>)", n32, ms32, by32
+        fam, n, kms, kbytes = "dslash_fp32 (hop3_kernel: TMA-fed FP32 hop)", n32, ms32, by32
     else:
         fam, n, kms, kbytes = "dslash_fp64 (hop_kernel<double>)", n64, ms64, by64
     achieved = kbytes / (kms / 1000.0) / 1e9 if kms else None

@@ -277,6 +277,26 @@ int laph_dirac_apply(laph_ctx *ctx, const laph_lattice *lat, const void *links,
                      const laph_dirac_params *dirac, const void *in, void *out, int nrhs,
                      void *stream);
 
+/* One even-odd hopping call with its fused site term, on half-lattice fields (the
+ * even-odd splitting of K used by the solvers, Sec. II; D = -1/2 sum_mu w_mu [...] as in
+ * laph_dirac_apply).  For output parity p (0 even, 1 odd) and q = 1 - p:
+ *   LAPH_HOP_CLOVINV       out = A_pp^{-1} D_pq in
+ *   LAPH_HOP_CLOVINV_XPAY  out = z - A_pp^{-1} D_pq in
+ *   LAPH_HOP_APPLY         out = A_pp z + D_pq in      (= (K x)_p with x_p = z, x_q = in)
+ * Half-lattice layout: [cb][spin*3 + colour][nrhs] complex, where cb = (lexicographic
+ * site index) / 2 runs over the Vh = V/2 sites of the field's parity and the right-hand
+ * side index is innermost.  precision LAPH_PREC_FP64: c128 fields, the FP64 kernel;
+ * LAPH_PREC_FP32: c64 fields, the packed-FP32 kernel of the mixed solver (links and
+ * clover rounded to FP32).  `z` may be NULL for LAPH_HOP_CLOVINV.  Host or device
+ * pointers; links [V][4][3][3] c128.  Returns after the stream has drained, so that a
+ * copy wait that gave up is reported (LAPH_ERR_TIMEOUT).  Errors: LAPH_ERR_ARG for a bad parity, mode or
+ * precision, nrhs < 1 or a missing pointer. */
+enum { LAPH_HOP_CLOVINV = 0, LAPH_HOP_CLOVINV_XPAY = 1, LAPH_HOP_APPLY = 2 };
+enum { LAPH_PREC_FP64 = 0, LAPH_PREC_FP32 = 1 };
+int laph_dslash_eo(laph_ctx *ctx, const laph_lattice *lat, const void *links, const laph_dirac_params *dirac,
+                   int parity, int mode, int precision, const void *in, const void *z, void *out, int nrhs,
+                   void *stream);
+
 /* ------------------------------------------------------------------------
  * (d) Sink coefficients (Sec. IV: the quark-propagation coefficients
  * V_s^dag Omega^{-1} V_s P^(b) rho, N_t N_v per spin):

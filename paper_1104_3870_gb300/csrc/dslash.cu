@@ -374,3 +374,40 @@ extern "C" int laph_dirac_apply(laph_ctx *ctx, const laph_lattice *lat, const vo
         o.commit(s);
     });
 }
+
+extern "C" int laph_dslash_eo(laph_ctx *ctx, const laph_lattice *lat, const void *links,
+                              const laph_dirac_params *dirac, int parity, int mode, int precision, const void *in,
+                              const void *z, void *out, int nrhs, void *stream) {
+    return guard([&] {
+        ctx_activate(ctx);
+        Geom g = make_geom(lat);
+        LAPH_REQUIRE(dirac != nullptr, "dirac params are null");
+        LAPH_REQUIRE(parity == 0 || parity == 1, "parity must be 0 or 1");
+        LAPH_REQUIRE(mode == LAPH_HOP_CLOVINV || mode == LAPH_HOP_CLOVINV_XPAY || mode == LAPH_HOP_APPLY,
+                     "unknown hop mode");
+        LAPH_REQUIRE(precision == LAPH_PREC_FP64 || precision == LAPH_PREC_FP32, "unknown precision");
+        LAPH_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+        LAPH_REQUIRE(in != nullptr && out != nullptr, "in/out are null");
+        LAPH_REQUIRE(mode == LAPH_HOP_CLOVINV || z != nullptr, "z is required in this mode");
+        cudaStream_t s = as_stream(stream);
+        const size_t elem = precision == LAPH_PREC_FP64 ? sizeof(c64) : sizeof(c32);
+        const size_t hb = elem * 12 * g.Vh * nrhs;
+        const c64 *L = (const c64 *)stage_in(ctx, links, sizeof(c64) * 36 * g.V, "links", s);
+        const void *x = stage_in(ctx, in, hb, "hop_in", s);
+        const void *zz = mode == LAPH_HOP_CLOVINV ? nullptr : stage_in(ctx, z, hb, "hop_z", s);
+        StagedOut o = stage_out(ctx, out, hb, "hop_out");
+        DiracOp op = prepare_dirac(ctx, g, L, dirac->m0, dirac->csw, lat->xi, s);
+        const HopMode hm = mode == LAPH_HOP_CLOVINV ? HOP_CLOVINV : mode == LAPH_HOP_CLOVINV_XPAY ? HOP_CLOVINV_XPAY
+                                                                                                : HOP_APPLY;
+        if (precision == LAPH_PREC_FP64) {
+            const c64 *zp = (const c64 *)zz;
+            hop<double>(op, parity, hm, (c64 *)o.dev, (const c64 *)x, hm == HOP_CLOVINV_XPAY ? zp : nullptr,
+                        hm == HOP_APPLY ? zp : nullptr, nrhs, s);
+        } else {
+            hop_f32(op, parity, hm, (c32 *)o.dev, (const c32 *)x, (const c32 *)zz, nrhs, s);
+        }
+        o.commit(s);
+        LAPH_CUDA(cudaStreamSynchronize(s));
+        hop_timeout_check();
+    });
+}

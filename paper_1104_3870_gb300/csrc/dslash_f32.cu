@@ -15,7 +15,13 @@
 //   L32w [p][mu][cb][9] float4 (re, re, im, im) of U_mu(x), row-major.
 //   C32w [p][cb][2 blocks][6 float2 (d, d) + 15 float4 (re, re, im, im)] (strictly lower part, row-major).
 // Thread mapping and spinor layout as in dslash.cu: thread (cb, r), f[cb][spin*3+colour][nr].
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdlib>
+
 #include "dirac.cuh"
+#include "tma.cuh"
 
 namespace laph {
 
@@ -25,9 +31,12 @@ __device__ __forceinline__ float2 rot_mi(float2 x) { return make_float2(x.y, -x.
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, ff(-b.x, -b.y)); }
+// operand load: read-only global path (G) or plain load (shared-memory staging)
+template <bool G, typename T>
+__device__ __forceinline__ T ld(const T *p) { return G ? __ldg(p) : *p; }
 
 // k[a] = sum_b U[a][b] h[b] (fwd) or sum_b conj(U[b][a]) h[b] (!fwd), two spin components.
-template <bool FWD>
+template <bool FWD, bool G = true>
 __device__ __forceinline__ void su3_mul2(const float4 *__restrict__ u, const float2 h0[3], const float2 h1[3],
                                          float2 k0[3], float2 k1[3]) {
     float2 r0[3], r1[3];
@@ -41,7 +50,7 @@ __device__ __forceinline__ void su3_mul2(const float4 *__restrict__ u, const flo
         float2 s0 = ff(0.f, 0.f), s1 = ff(0.f, 0.f);
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            float4 e = __ldg(u + (FWD ? a * 3 + b : b * 3 + a));
+            float4 e = ld<G>(u + (FWD ? a * 3 + b : b * 3 + a));
             float2 rr = ff(e.x, e.y), ii = ff(e.z, e.w);
             s0 = fma2(rr, h0[b], s0);
             s0 = fma2(ii, r0[b], s0);
@@ -55,7 +64,7 @@ __device__ __forceinline__ void su3_mul2(const float4 *__restrict__ u, const flo
 
 // One direction: project the neighbour spinor, multiply by the link, accumulate with weight c.
 // FWD: (1 - gamma_mu) U psi(x+mu);  !FWD: (1 + gamma_mu) U^dag psi(x-mu).
-template <int MU, bool FWD>
+template <int MU, bool FWD, bool G = true>
 __device__ __forceinline__ void hop_dir2(float2 acc[12], const float2 *__restrict__ src, int nr,
                                          const float4 *__restrict__ u, float c) {
     float2 h0[3], h1[3];
@@ -79,7 +88,7 @@ __device__ __forceinline__ void hop_dir2(float2 acc[12], const float2 *__restric
         }
     }
     float2 k0[3], k1[3];
-    su3_mul2<FWD>(u, h0, h1, k0, k1);
+    su3_mul2<FWD, G>(u, h0, h1, k0, k1);
     const float2 cc = ff(c, c);
 #pragma unroll
     for (int col = 0; col < 3; ++col) {
@@ -99,13 +108,14 @@ __device__ __forceinline__ void hop_dir2(float2 acc[12], const float2 *__restric
 }
 
 // y = B x for one packed Hermitian 6x6 block: 6 float2 (d, d) then 15 float4 (re, re, im, im).
+template <bool G = true>
 __device__ __forceinline__ void herm6_f2(const float *__restrict__ blk, const float2 x[6], float2 y[6]) {
     const float2 *dg = reinterpret_cast<const float2 *>(blk);
     const float4 *lo = reinterpret_cast<const float4 *>(blk + 12);
     float2 ix[6], mix[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        y[i] = __fmul2_rn(__ldg(dg + i), x[i]);
+        y[i] = __fmul2_rn(ld<G>(dg + i), x[i]);
         ix[i] = rot_i(x[i]);
         mix[i] = rot_mi(x[i]);
     }
@@ -114,7 +124,7 @@ __device__ __forceinline__ void herm6_f2(const float *__restrict__ blk, const fl
     for (int i = 1; i < 6; ++i)
 #pragma unroll
         for (int j = 0; j < i; ++j) {
-            float4 e = __ldg(lo + o++);
+            float4 e = ld<G>(lo + o++);
             float2 rr = ff(e.x, e.y), ii = ff(e.z, e.w);
             y[i] = fma2(rr, x[j], y[i]);
             y[i] = fma2(ii, ix[j], y[i]);
@@ -124,7 +134,7 @@ __device__ __forceinline__ void herm6_f2(const float *__restrict__ blk, const fl
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(128) hop2_kernel(const int *__restrict__ nbr, const float4 *__restrict__ L,
+__global__ void __launch_bounds__(128, MODE == HOP_APPLY ? 6 : 8) hop2_kernel(const int *__restrict__ nbr, const float4 *__restrict__ L,
                                                    const float *__restrict__ C, long Vh, int p, float hws, float hwt,
                                                    float2 *__restrict__ out, const float2 *__restrict__ in,
                                                    const float2 *__restrict__ z, int nr) {
@@ -185,6 +195,258 @@ __global__ void __launch_bounds__(128) hop2_kernel(const int *__restrict__ nbr, 
     }
 }
 
+// ------------------------------------------------------------------ TMA-fed hop
+// The same arithmetic as hop2_kernel, with the operands of every hop brought into shared
+// memory by the copy engine ahead of use.  A work unit is one warp: 32 right-hand sides of
+// one output site (nr = 32 * 2^k).  It consumes nine jobs in order — the eight hops
+// (forward mu = 0, backward mu = 0, forward mu = 1, ...) and an epilogue — each filling one
+// slot of the warp's private ring of NS slots:
+//   hop job       [12][32] float2 tile of the neighbour spinor (one 2D tensor copy) + 9 float4 link
+//   epilogue job  [12][32] float2 tile of z (modes with z) + the 144-float clover block of the site
+// While the warp computes job n, jobs n+1 .. n+NS-1 are in flight; the slot of job n is
+// refilled with job n+NS as soon as every lane has read it.  Lane 0 issues all copies, so a
+// job costs the warp a handful of instructions, and warps never wait on one another.
+constexpr int HOP3_WARPS = 4;
+constexpr int HOP3_SLOT = 3712;            // 29 x 128 B: 3072 B spinor tile + 144 B link or 576 B clover
+constexpr int HOP3_SPIN = 3072;
+constexpr long long HOP3_WAIT_CYCLES = 1LL << 31;   // about one second at the maximum SM clock
+
+__device__ int g_hop3_timeout;   // set when a copy wait gives up (or the ring is misaligned); read by the host
+
+template <int MODE, int NS>
+__global__ void __launch_bounds__(HOP3_WARPS * 32)
+    hop3_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_z,
+                const int *__restrict__ nbr, const float4 *__restrict__ L, const float *__restrict__ C, int Vh, int p,
+                float hws, float hwt, float2 *__restrict__ out, int nr, int gshift, int nunits) {
+    extern __shared__ __align__(128) unsigned char sm3[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (smem_u32(sm3) & 127) {   // tensor copies need 128-byte aligned destinations
+        if (threadIdx.x == 0) atomicExch(&g_hop3_timeout, 2);
+        return;
+    }
+    unsigned char *ring = sm3 + warp * NS * HOP3_SLOT;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm3 + HOP3_WARPS * NS * HOP3_SLOT) + warp * NS;
+    float *meta = reinterpret_cast<float *>(sm3 + HOP3_WARPS * NS * (HOP3_SLOT + 8)) + warp * NS;
+    if (lane < NS) mbar_init(bar + lane, 1);
+    mbar_fence_init();
+    __syncwarp();
+    const int gmask = (1 << gshift) - 1;
+    const int gw = blockIdx.x * HOP3_WARPS + warp, gstride = gridDim.x * HOP3_WARPS;
+    const int nu = gw < nunits ? (nunits - gw + gstride - 1) / gstride : 0;
+    const int *nbp = nbr + (long)p * Vh * 8;
+
+    // issue pointer: job ij of the unit iq (the ik-th of this warp) goes to slot islot; lane
+    // d < 8 holds neighbour d of unit iq (nb_i) and of the unit after it (nb_n)
+    int iq = gw, ik = 0, ij = 0, islot = 0, niss = 0;
+    int nb_i = (nu > 0 && lane < 8) ? __ldg(nbp + (iq >> gshift) * 8 + lane) : 0;
+    int nb_n = (nu > 1 && lane < 8) ? __ldg(nbp + ((iq + gstride) >> gshift) * 8 + lane) : 0;
+    auto issue = [&]() {
+        if (ik >= nu) return;
+        const int e = __shfl_sync(0xffffffffu, nb_i, (ij & 1) ? 4 + (ij >> 1) : (ij >> 1));
+        if (lane == 0) {
+            const int cb = iq >> gshift, h = iq & gmask;
+            unsigned char *sl = ring + islot * HOP3_SLOT;
+            uint64_t *b = bar + islot;
+            fence_proxy_async_smem();
+            if (ij < 8) {
+                const int mu = ij >> 1;
+                const float w = mu == 3 ? hwt : hws;
+                const int jn = e < 0 ? ~e : e;
+                meta[islot] = e < 0 ? -w : w;
+                mbar_arrive_expect_tx(b, HOP3_SPIN + 144);
+                tma_tile_2d(sl, &tm_in, 64 * h, 12 * jn, b);
+                const float4 *u = (ij & 1) ? L + ((long)((1 - p) * 4 + mu) * Vh + jn) * 9
+                                           : L + ((long)(p * 4 + mu) * Vh + cb) * 9;
+                bulk_g2s(sl + HOP3_SPIN, u, 144, b);
+            } else {
+                constexpr bool needz = MODE != HOP_CLOVINV;
+                mbar_arrive_expect_tx(b, (needz ? HOP3_SPIN : 0) + 576);
+                if (needz) tma_tile_2d(sl, &tm_z, 64 * h, 12 * cb, b);
+                bulk_g2s(sl + HOP3_SPIN, C + ((long)p * Vh + cb) * 144, 576, b);
+            }
+        }
+        ++niss;
+        if (++islot == NS) islot = 0;
+        if (++ij == 9) {
+            ij = 0;
+            ++ik;
+            iq += gstride;
+            nb_i = nb_n;
+            nb_n = (ik + 1 < nu && lane < 8) ? __ldg(nbp + ((iq + gstride) >> gshift) * 8 + lane) : 0;
+        }
+    };
+    // consume pointer
+    int cslot = 0, ncons = 0;
+    uint32_t cpar = 0;
+    auto wait = [&]() -> bool {
+        return __all_sync(0xffffffffu, mbar_wait_bounded(bar + cslot, cpar, HOP3_WAIT_CYCLES));
+    };
+    auto release = [&]() {
+        __syncwarp();
+        issue();
+        ++ncons;
+        if (++cslot == NS) {
+            cslot = 0;
+            cpar ^= 1u;
+        }
+    };
+
+    for (int k = 0; k < NS; ++k) issue();
+    bool ok = true;
+    for (int k = 0, q = gw; k < nu && ok; ++k, q += gstride) {
+        const int cb = q >> gshift, h = q & gmask;
+        float2 acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = ff(0.f, 0.f);
+#define HOP3_DIR(MU, FWD)                                                                                 \
+    if (ok) {                                                                                             \
+        if (!wait()) {                                                                                    \
+            ok = false;                                                                                   \
+        } else {                                                                                          \
+            const unsigned char *sl_ = ring + cslot * HOP3_SLOT;                                          \
+            hop_dir2<MU, FWD, false>(acc, reinterpret_cast<const float2 *>(sl_) + lane, 32,               \
+                                     reinterpret_cast<const float4 *>(sl_ + HOP3_SPIN), meta[cslot]);     \
+            release();                                                                                    \
+        }                                                                                                 \
+    }
+        HOP3_DIR(0, true)
+        HOP3_DIR(0, false)
+        HOP3_DIR(1, true)
+        HOP3_DIR(1, false)
+        HOP3_DIR(2, true)
+        HOP3_DIR(2, false)
+        HOP3_DIR(3, true)
+        HOP3_DIR(3, false)
+#undef HOP3_DIR
+        if (!ok || !wait()) {
+            ok = false;
+            break;
+        }
+        const unsigned char *sl = ring + cslot * HOP3_SLOT;
+        const float *cl = reinterpret_cast<const float *>(sl + HOP3_SPIN);
+        const float2 *zs = reinterpret_cast<const float2 *>(sl) + lane;
+        float2 res[12];
+        if (MODE == HOP_APPLY) {
+            float2 xv[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) xv[c] = zs[c * 32];
+            herm6_f2<false>(cl, xv, res);
+            herm6_f2<false>(cl + 72, xv + 6, res + 6);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) res[c] = add2(res[c], acc[c]);
+        } else {
+            herm6_f2<false>(cl, acc, res);
+            herm6_f2<false>(cl + 72, acc + 6, res + 6);
+            if (MODE == HOP_CLOVINV_XPAY) {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) res[c] = sub2(zs[c * 32], res[c]);
+            }
+        }
+        release();
+        float2 *dst = out + (long)cb * 12 * nr + 32 * h + lane;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) dst[(long)c * nr] = res[c];
+    }
+    if (!ok) {
+        if (lane == 0) atomicExch(&g_hop3_timeout, 1);
+        // wait (bounded) for every job issued and not yet read, so no copy lands after exit
+        for (; ncons < niss; ++ncons) {
+            mbar_wait_bounded(bar + cslot, cpar, HOP3_WAIT_CYCLES);
+            if (++cslot == NS) {
+                cslot = 0;
+                cpar ^= 1u;
+            }
+        }
+    }
+}
+
+// 2D view of a half-lattice FP32 field [cb][12][nr] complex: rows (cb, component) of 2 nr
+// floats; a box is the 12 rows x 32 right-hand sides that one warp reads.
+static CUtensorMap spinor_map(const float2 *base, long Vh, int nr) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        LAPH_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        LAPH_REQUIRE(q == cudaDriverEntryPointSuccess && fn != nullptr, "cuTensorMapEncodeTiled is unavailable");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * nr), (cuuint64_t)(12 * Vh)};
+    const cuuint64_t strides[1] = {(cuuint64_t)(2 * nr) * sizeof(float)};
+    const cuuint32_t box[2] = {64, 12};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    LAPH_REQUIRE(r == CUDA_SUCCESS, "tensor map encoding failed");
+    return m;
+}
+
+template <int MODE, int NS>
+static void launch_hop3(const DiracOp &op, int p, float hws, float hwt, float2 *out, const float2 *in,
+                        const float2 *z, int nr, cudaStream_t s) {
+    constexpr size_t smem = (size_t)HOP3_WARPS * NS * (HOP3_SLOT + 8 + 4);
+    static int bpsm[64] = {0};
+    static int nsm[64] = {0};
+    int dev = 0;
+    LAPH_CUDA(cudaGetDevice(&dev));
+    LAPH_REQUIRE(dev < 64, "device index out of range");
+    if (bpsm[dev] == 0) {
+        LAPH_CUDA(cudaFuncSetAttribute(hop3_kernel<MODE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LAPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm[dev], hop3_kernel<MODE, NS>, HOP3_WARPS * 32,
+                                                                smem));
+        LAPH_CUDA(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
+        LAPH_REQUIRE(bpsm[dev] > 0, "TMA hop kernel does not fit on this device");
+    }
+    int gshift = 0;
+    while ((32 << gshift) < nr) ++gshift;
+    const CUtensorMap tin = spinor_map(in, op.g.Vh, nr);
+    const CUtensorMap tz = MODE == HOP_CLOVINV ? tin : spinor_map(z, op.g.Vh, nr);
+    const long nunits = op.g.Vh * (nr / 32);
+    long grid = (nunits + HOP3_WARPS - 1) / HOP3_WARPS;
+    const long cap = (long)bpsm[dev] * nsm[dev];
+    if (grid > cap) grid = cap;
+    hop3_kernel<MODE, NS><<<(unsigned)grid, HOP3_WARPS * 32, smem, s>>>(
+        tin, tz, op.nbr, op.L32w, MODE == HOP_APPLY ? op.C32wA : op.C32w, (int)op.g.Vh, p, hws, hwt, out, nr, gshift,
+        (int)nunits);
+}
+
+// Ring depth per warp of the TMA-fed kernel.  Two slots measured fastest on a 16^3 x 32
+// lattice at 32 and 64 right-hand sides: a deeper ring costs more occupancy than its extra
+// prefetch gains.  LAPH_HOP_STAGES = 3, 4 or 6 selects a deeper ring, 0 the register-fed
+// kernel (hop2_kernel) for every shape.
+static int hop3_stages() {
+    static int ns = -1;
+    if (ns < 0) {
+        const char *e = getenv("LAPH_HOP_STAGES");
+        int v = e ? atoi(e) : 2;
+        ns = (v == 0 || v == 2 || v == 3 || v == 4 || v == 6) ? v : 2;
+    }
+    return ns;
+}
+
+template <int NS>
+static void hop3_modes(const DiracOp &op, int p, HopMode mode, float hws, float hwt, float2 *out, const float2 *in,
+                       const float2 *z, int nr, cudaStream_t s) {
+    if (mode == HOP_APPLY)
+        launch_hop3<HOP_APPLY, NS>(op, p, hws, hwt, out, in, z, nr, s);
+    else if (mode == HOP_CLOVINV)
+        launch_hop3<HOP_CLOVINV, NS>(op, p, hws, hwt, out, in, nullptr, nr, s);
+    else
+        launch_hop3<HOP_CLOVINV_XPAY, NS>(op, p, hws, hwt, out, in, z, nr, s);
+}
+
+void hop_timeout_check() {
+    int v = 0;
+    LAPH_CUDA(cudaMemcpyFromSymbol(&v, g_hop3_timeout, sizeof(int)));
+    if (v) {   // 1: a copy wait gave up; 2: the shared-memory ring was misaligned (no copy issued)
+        const int zero = 0;
+        LAPH_CUDA(cudaMemcpyToSymbol(g_hop3_timeout, &zero, sizeof(int)));
+        throw Error(LAPH_ERR_TIMEOUT, "a stencil copy wait gave up (device wait cap)");
+    }
+}
+
 double hop_bytes(const DiracOp &op, HopMode mode, int nr, size_t real_bytes);
 double hop_flops(const DiracOp &op, int nr);
 
@@ -196,7 +458,21 @@ void hop_f32(const DiracOp &op, int p, HopMode mode, c32 *out, const c32 *in, co
     unsigned grid = grid_for(n, block);
     float hws = (float)op.hw[0], hwt = (float)op.hw[3];
     prof_begin("dslash_fp32", s);
-    if (mode == HOP_APPLY)
+    const bool aligned = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(z) |
+                           reinterpret_cast<uintptr_t>(op.L32w) | reinterpret_cast<uintptr_t>(op.C32w) |
+                           reinterpret_cast<uintptr_t>(op.C32wA)) & 15) == 0;
+    const int ns = hop3_stages();
+    const bool pow2 = nr == 32 || nr == 64 || nr == 128 || nr == 256;
+    if (pow2 && aligned && ns > 0 && op.g.Vh * (nr / 32) < (1L << 30)) {
+        float2 *o = (float2 *)out;
+        const float2 *i = (const float2 *)in, *zz = (const float2 *)z;
+        switch (ns) {
+            case 3: hop3_modes<3>(op, p, mode, hws, hwt, o, i, zz, nr, s); break;
+            case 6: hop3_modes<6>(op, p, mode, hws, hwt, o, i, zz, nr, s); break;
+            case 4: hop3_modes<4>(op, p, mode, hws, hwt, o, i, zz, nr, s); break;
+            default: hop3_modes<2>(op, p, mode, hws, hwt, o, i, zz, nr, s); break;
+        }
+    } else if (mode == HOP_APPLY)
         hop2_kernel<HOP_APPLY><<<grid, block, 0, s>>>(op.nbr, op.L32w, op.C32wA, op.g.Vh, p, hws, hwt, (float2 *)out,
                                                       (const float2 *)in, (const float2 *)z, nr);
     else if (mode == HOP_CLOVINV)

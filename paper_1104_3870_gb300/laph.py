@@ -21,6 +21,8 @@ LAPH_OK, LAPH_ERR_ARG, LAPH_ERR_CUDA, LAPH_ERR_NOT_CONVERGED, LAPH_ERR_TIMEOUT, 
 PLAIN_FP64, MIXED_FP32, MIXED_BF16, LEARNED = range(4)
 CH_PION, CH_RHO, CH_SCALAR, CH_PIPI_I2 = range(4)
 DIL_NONE, DIL_FULL, DIL_BLOCK, DIL_INTERLACE = range(4)
+HOP_CLOVINV, HOP_CLOVINV_XPAY, HOP_APPLY = range(3)
+PREC_FP64, PREC_FP32 = range(2)
 
 
 class LaphError(RuntimeError):
@@ -89,6 +91,8 @@ _sig = {
                                          ctypes.c_int, ctypes.POINTER(SolverParams), _vp, _vp]),
     "laph_dirac_apply": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), _vp, _vp,
                                         ctypes.c_int, _vp]),
+    "laph_dslash_eo": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "laph_sinks": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "correlate": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
     "correlate_noalloc": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
@@ -247,6 +251,12 @@ def dirac_solve_batch(ctx, lat, links, m0, csw, rhs, sol, nrhs, params=None, str
 def laph_dirac_apply(ctx, lat, links, m0, csw, inp, out, nrhs, stream=None):
     _check(_lib.laph_dirac_apply(ctx.ptr, ctypes.byref(lat), _ptr(links), ctypes.byref(DiracParams(m0, csw)),
                                  _ptr(inp), _ptr(out), int(nrhs), _stream(stream)))
+
+
+def laph_dslash_eo(ctx, lat, links, m0, csw, parity, mode, precision, inp, z, out, nrhs, stream=None):
+    _check(_lib.laph_dslash_eo(ctx.ptr, ctypes.byref(lat), _ptr(links), ctypes.byref(DiracParams(m0, csw)),
+                               int(parity), int(mode), int(precision), _ptr(inp), _ptr(z), _ptr(out), int(nrhs),
+                               _stream(stream)))
 
 
 def laph_sinks(ctx, lat, evecs, nv, sol, nrhs, coef, stream=None):
