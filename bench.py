@@ -7,13 +7,20 @@ Laplacian eigenvectors of every slice (a1), Z4 diluted sources for two noises
 (a3), sink coefficients (a4) and the pion / scalar / rho correlators (a5).
 Gauge preparation (stout smearing, a0) is setup and not timed.
 
-Default workload: 16^3 x 32, xi = 3.5, N_v = 32, (TF, SF, LI8) at t0 = 0, two
-noises -> 64 diluted sources per step (seeded synthetic gauge field).
+Default workload: 16^3 x 32, xi = 3.5, N_v = 32, (TF, SF, LI8) at four source
+times (0, 8, 16, 24), two noises -> 256 diluted sources per step (seeded synthetic
+gauge field).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
 replica (its own noises); value = sources of all ranks / max rank time.
+
+    python bench.py --dslash-sweep [--dslash-nr 1,8,16,32,64] [--dslash-iters 50]
+
+prints the Dslash half of the metric instead: the even-odd hop's algorithmic HBM GB/s
+at several right-hand-side counts, FP32 (inner solver) and FP64, timed with CUDA events
+around every hop launch inside solver iterations on the workload's lattice.
 """
 import argparse
 import json
@@ -44,6 +51,10 @@ def parse_args(argv=None):
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per solver launch (0: all)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--dslash-sweep", action="store_true", help="print the Dslash GB/s sweep instead of the path step")
+    p.add_argument("--dslash-nr", default="1,8,16,32,64", help="right-hand-side counts of the Dslash sweep")
+    p.add_argument("--dslash-iters", type=int, default=50, help="solver iterations per sweep point")
+    p.add_argument("--dslash-prec", default="fp32,fp64", help="precisions of the Dslash sweep")
     return p.parse_args(argv)
 
 
@@ -413,9 +424,64 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dslash_sweep(args):
+    """Hop launches inside `--dslash-iters` BiCGStab iterations of a block of nr random
+    right-hand sides (the solve stops early, by design, before it converges), averaged
+    per launch by the library's event timer.  Algorithmic bytes per launch: 48 reals of
+    spinor per site and RHS (read 24, write 24) plus 8 links x 12 reals and 72 clover
+    reals per site (FP32 or FP64 reals), as the library's hop_bytes counts them; the XPAY
+    launches read z as well.  Rows whose solver working set fits in L2 say so."""
+    import torch
+    from paper_1104_3870_gb300 import build
+    build.build()
+    from paper_1104_3870_gb300 import laph as L
+    from paper_1104_3870_gb300.pipeline import LapHPath, LatticeSpec
+    import synth
+
+    wl = synth.WORKLOADS[args.workload]
+    spec = LatticeSpec(wl.ns, wl.nt, wl.xi, wl.m0, wl.csw, wl.nv, (wl.dil_time, wl.dil_spin, wl.dil_laph),
+                       wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
+    path = LapHPath(spec, 0)
+    u, _ = path.prepare_links(wl.gauge())
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    l2_bytes = 129e6
+    vh = wl.ns ** 3 * wl.nt // 2
+    rows = []
+    for prec in args.dslash_prec.split(","):
+        mode, fam, real = ((L.MIXED_FP32, "dslash_fp32", 4) if prec == "fp32" else (L.PLAIN_FP64, "dslash_fp64", 8))
+        for nr in [int(v) for v in args.dslash_nr.split(",")]:
+            b = torch.randn((nr, wl.nt, wl.ns, wl.ns, wl.ns, 4, 3), dtype=torch.complex128, device="cuda")
+            x = torch.empty_like(b)
+            prm = L.solver_params(tol=1e-14, maxiter=args.dslash_iters, mode=mode, rhs_block=nr,
+                                  inner_tol=1e-14)
+            L.laph_profile_reset()
+            L.laph_profile_enable(1)
+            L.dirac_solve_batch(path.ctx, path.lat, u, wl.m0, wl.csw, b, x, nr, prm, allow_not_converged=True)
+            torch.cuda.synchronize()
+            L.laph_profile_enable(0)
+            n, ms, by, fl = L.laph_profile_read(fam)
+            gbs = by / (ms / 1000.0) / 1e9 if ms else None
+            working = 8 * vh * 12 * nr * 2 * real            # about eight half-lattice solver vectors
+            rows.append({"precision": prec, "nr": nr, "launches": n, "avg_launch_us": 1000.0 * ms / n if n else None,
+                         "algorithmic_bytes_per_launch": by / n if n else None, "GBs": gbs,
+                         "frac": gbs / hbm if gbs else None, "gflops": fl / (ms / 1000.0) / 1e9 if ms else None,
+                         "l2_resident": working < l2_bytes,
+                         "kernel": ("hop3_kernel (TMA-fed)" if prec == "fp32" and nr % 32 == 0 and nr & (nr - 1) == 0
+                                    else "hop2_kernel" if prec == "fp32" else "hop_kernel<double>")})
+            del b, x
+    print(json.dumps({"metric": "Dslash HBM GB/s (algorithmic bytes / event-timed launch)", "unit": "GB/s",
+                      "workload": wl.name, "lattice": f"{wl.ns}^3x{wl.nt}", "peak": hbm,
+                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                      "rows": rows}), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
-    if args.impl == "reference":
+    if args.dslash_sweep:
+        run_dslash_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
