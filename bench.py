@@ -87,6 +87,12 @@ def whole_job_rate(units_per_rank, world, max_seconds):
     return units_per_rank * world / max_seconds
 
 
+def replica_noise_ids(rank, nnoise):
+    """Noise ids of one replica: rank r draws noises r*nnoise .. r*nnoise + nnoise - 1, so no
+    two ranks solve the same diluted source (Z4 noise is a pure function of the id)."""
+    return [rank * nnoise + k for k in range(nnoise)]
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -202,7 +208,7 @@ class PathStep:
         self.nb = len(self.bss[0])
         self.nnoise = wl.n_noise
         self.nsrc = len(self.t0s) * self.nnoise * self.nb
-        self.noise_ids = [rank * self.nnoise + k for k in range(self.nnoise)]
+        self.noise_ids = replica_noise_ids(rank, self.nnoise)
         self.rhs = path.field(self.nsrc)
         self.sol = torch.empty_like(self.rhs)
         self.coef = torch.empty((self.nsrc, wl.nt, 4, wl.nv), dtype=torch.complex128, device="cuda")

@@ -194,14 +194,20 @@ int laph_make_sources(laph_ctx *ctx, const laph_lattice *lat, const void *evecs,
  *                          (rhs_block = 1 is the one-at-a-time baseline).
  *   LAPH_SOLVE_MIXED_FP32  FP64 defect correction around FP32 even-odd
  *                          BiCGStab, all RHS of a block in one launch.
- *   LAPH_SOLVE_MIXED_BF16  as MIXED_FP32 with BF16 storage of the inner
- *                          stencil operands (FP32 arithmetic).
+ *   LAPH_SOLVE_MIXED_BF16  reserved for BF16 storage of the inner stencil
+ *                          operands; not available in this version (LAPH_ERR_ARG).
  *   LAPH_SOLVE_LEARNED     FP64 defect correction around FP32 flexible GCR
  *                          with the learned right preconditioner `weights`
  *                          (layout of laph_precond_train).
- * A right-hand side that stalls (no 10x residual drop in 200 inner
- * iterations, or BiCGStab breakdown) is finished by FP64 CG on K^dag K
- * when params->fallback is nonzero; report[i].fallback_used is set.
+ * Sec. IV: where BiCGStab does not converge, a CG solve of the normal
+ * equations finishes the system.  Here (params->fallback nonzero, PLAIN and
+ * MIXED modes) a right-hand side still above tol when the inner budget
+ * (maxiter) or 100 defect-correction cycles are spent, or whose true residual
+ * fell by less than 2x in each of three consecutive cycles, is finished by
+ * FP64 CG on K^dag K e = K^dag r (K^dag = gamma_5 K gamma_5); report[i].iters
+ * then includes the CG iterations and report[i].fallback_used = 1.  In
+ * LEARNED mode a stalled flexible-GCR cycle hands the right-hand side to the
+ * MIXED solver instead (fallback_used = 1).
  * ------------------------------------------------------------------------ */
 enum {
     LAPH_SOLVE_PLAIN_FP64 = 0,
@@ -221,7 +227,7 @@ typedef struct {
     int mode;              /* LAPH_SOLVE_*                                          */
     int rhs_block;         /* RHS per launch (<= 0: autotuned)                     */
     double inner_tol;      /* inner relative tolerance per cycle (<= 0: 1e-5)      */
-    int fallback;          /* 1: CG on the normal equations after a stall          */
+    int fallback;          /* 1: finish stalled RHS with the fallback solver        */
     const float *weights;  /* LEARNED only: preconditioner weights (device/host)   */
     int gcr_restart;       /* LEARNED only: FGCR restart length (<= 0: 16)         */
     int check_every;       /* iterations between host convergence checks (<= 0: 25)*/
@@ -231,7 +237,7 @@ typedef struct {
     int iters;             /* inner iterations (Schur-operator applications / 2)   */
     int outer;             /* defect-correction cycles                              */
     int status;            /* LAPH_OK or LAPH_ERR_NOT_CONVERGED                     */
-    int fallback_used;     /* 1 if the CG fallback ran                              */
+    int fallback_used;     /* 1 if the fallback solver ran for this RHS            */
     double true_resid;     /* final ||b - K x|| / ||b|| in FP64                     */
 } laph_solve_report;
 

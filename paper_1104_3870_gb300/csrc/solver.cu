@@ -100,7 +100,14 @@ static InnerStats bicgstab_schur(laph_ctx *ctx, const DiracOp &op, int nr, const
     return st;
 }
 
+std::vector<int> cgnr_solve(laph_ctx *ctx, const DiracOp &op, int nr, c64 *r, c64 *e,
+                            const std::vector<double> &target, int maxiter, int check_every, std::vector<int> &conv,
+                            cudaStream_t s);
+
 // Solves one block of nr right-hand sides, columns [first, first+nr) of the ABI arrays.
+// A right-hand side still above the tolerance when the inner budget or the cycle limit is
+// spent, or whose residual fell by less than a factor 2 in each of three consecutive
+// defect-correction cycles, is finished by FP64 CG on the normal equations (params.fallback).
 void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int first, int nr,
                         const laph_solver_params &prm, laph_solve_report *rep, cudaStream_t s) {
     const Geom &g = op.g;
@@ -130,7 +137,8 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
     LAPH_CUDA(cudaMemsetAsync(xe, 0, hb, s));
     const double tol = prm.tol;
     std::vector<double> rel(nr, 1.0);
-    std::vector<int> iters(nr, 0), outer(nr, 0), broke(nr, 0);
+    std::vector<int> iters(nr, 0), outer(nr, 0), broke(nr, 0), stall(nr, 0), handed(nr, 0), fell(nr, 0);
+    std::vector<double> prev(nr, 1.0);
     int total_iters = 0;
     const int max_outer = 100;
     for (int cyc = 0; cyc <= max_outer; ++cyc) {
@@ -160,9 +168,14 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
                 double rn = std::sqrt(h_red[k].re + h_red[nr + k].re);
                 rel[k] = bnorm[k] > 0 ? rn / bnorm[k] : 0.0;
                 if (!(rel[k] <= tol)) {
-                    all = false;
-                    worst = std::max(worst, std::isfinite(rel[k]) ? rel[k] : 1e300);
+                    stall[k] = (cyc > 1 && !(rel[k] <= 0.5 * prev[k])) ? stall[k] + 1 : 0;
+                    if (prm.fallback && stall[k] >= 3) handed[k] = 1;
+                    if (!handed[k]) {
+                        all = false;
+                        worst = std::max(worst, std::isfinite(rel[k]) ? rel[k] : 1e300);
+                    }
                 }
+                prev[k] = rel[k];
             }
             if (all || cyc == max_outer || total_iters >= prm.maxiter) break;
             // With x_o reconstructed from x_e the Schur residual bhat - M x_e equals A_ee^{-1} r_e.
@@ -174,7 +187,7 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
         LAPH_CUDA(cudaStreamSynchronize(s));
         for (int k = 0; k < nr; ++k) {
             double rn = std::sqrt(h_red[k].re);
-            bool done = rel[k] <= tol || !(rn > 0.0) || !std::isfinite(rn);
+            bool done = rel[k] <= tol || handed[k] || !(rn > 0.0) || !std::isfinite(rn);
             h_scale[k] = done ? 0.0 : 1.0 / rn;   // into the inner precision
             h_scale[nr + k] = done ? 0.0 : rn;    // back into x_e
             if (!done) outer[k] += 1;
@@ -207,6 +220,40 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
         }
         total_iters += mx;
     }
+    // re, ro hold the true residual b - K x of the current (xe, xo) here: every exit from the
+    // cycle loop after cycle 0 comes right after it is computed, and cycle 0 exits only when
+    // every right-hand side is zero.
+    bool need = false;
+    for (int k = 0; k < nr; ++k) need |= !(rel[k] <= tol);
+    if (prm.fallback && need) {
+        const long half = nrows * nr;
+        c64 *rp = (c64 *)ws_get(ctx, "dc:cg_r", 2 * hb), *ep = (c64 *)ws_get(ctx, "dc:cg_e", 2 * hb);
+        std::vector<double> target(nr, 0.0), mask(2 * nr, 0.0);
+        for (int k = 0; k < nr; ++k) {
+            fell[k] = !(rel[k] <= tol) && std::isfinite(rel[k]);
+            target[k] = fell[k] ? 0.5 * tol * bnorm[k] : 0.0;
+            mask[k] = fell[k] ? 1.0 : 0.0;
+            mask[nr + k] = 1.0;
+        }
+        LAPH_CUDA(cudaMemcpyAsync(scale, mask.data(), sizeof(double) * 2 * nr, cudaMemcpyHostToDevice, s));
+        mrhs_copy_scaled<double, double>(nrows, nr, scale, re, rp, s);
+        mrhs_copy_scaled<double, double>(nrows, nr, scale, ro, rp + half, s);
+        std::vector<int> conv;
+        std::vector<int> cg_it = cgnr_solve(ctx, op, nr, rp, ep, target, 20000, prm.check_every, conv, s);
+        mrhs_axpy_scaled<double, double>(nrows, nr, scale + nr, ep, xe, s);
+        mrhs_axpy_scaled<double, double>(nrows, nr, scale + nr, ep + half, xo, s);
+        // the true residual of the corrected solution
+        hop<double>(op, 0, HOP_RESID, re, xo, be, xe, nr, s);
+        hop<double>(op, 1, HOP_RESID, ro, xe, bo, xo, nr, s);
+        mrhs_dots<double>(ctx, pl, nrows, 2, re, re, ro, ro, nullptr, nullptr, red, s);
+        LAPH_CUDA(cudaMemcpyAsync(h_red.data(), red, sizeof(c64) * 2 * nr, cudaMemcpyDeviceToHost, s));
+        LAPH_CUDA(cudaStreamSynchronize(s));
+        for (int k = 0; k < nr; ++k) {
+            if (!fell[k]) continue;
+            rel[k] = bnorm[k] > 0 ? std::sqrt(h_red[k].re + h_red[nr + k].re) / bnorm[k] : 0.0;
+            iters[k] += cg_it[k];
+        }
+    }
     eo_to_fields(g, xe, xo, first, nr, sol, s);
     if (rep) {
         for (int k = 0; k < nr; ++k) {
@@ -215,7 +262,7 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
             o.outer = outer[k];
             o.true_resid = rel[k];
             o.status = rel[k] <= tol ? LAPH_OK : LAPH_ERR_NOT_CONVERGED;
-            o.fallback_used = 0;
+            o.fallback_used = fell[k];
         }
     }
 }

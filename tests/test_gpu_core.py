@@ -86,6 +86,30 @@ def test_solve_vs_dense_lu(tiny, mode):
         assert reps[i].iters > 0
 
 
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_solve_cg_fallback(tiny, mode):
+    """A Krylov budget far too small for BiCGStab (a host-side injected failure) hands every
+    right-hand side to the FP64 CG solve of the normal equations (Sec. IV), which must still
+    meet the tolerance; without the fallback the call reports non-convergence."""
+    L = lib()
+    wl = tiny.wl
+    b = synth.random_spinor(wl.ns, wl.nt, seed=57, nrhs=3)
+    x_lu, _ = tiny.solve(b, "lu")
+    m = L.PLAIN_FP64 if mode == "plain" else L.MIXED_FP32
+    lat = L.lattice(wl.ns, wl.nt, wl.xi)
+    sol = empty(b.shape, dev(b).dtype)
+    reps = L.dirac_solve_batch(context(), lat, dev(tiny.u), wl.m0, wl.csw, dev(b), sol, 3,
+                               L.solver_params(tol=1e-10, mode=m, maxiter=10, fallback=1))
+    x = host(sol)
+    for i in range(3):
+        assert reps[i].fallback_used == 1 and reps[i].status == 0
+        assert reps[i].true_resid <= 1e-10
+        assert np.linalg.norm(x[i] - x_lu[i]) / np.linalg.norm(x_lu[i]) < 1e-8
+    reps = L.dirac_solve_batch(context(), lat, dev(tiny.u), wl.m0, wl.csw, dev(b), sol, 3,
+                               L.solver_params(tol=1e-10, mode=m, maxiter=10, fallback=0), allow_not_converged=True)
+    assert all(r.fallback_used == 0 and r.status == L.LAPH_ERR_NOT_CONVERGED for r in reps)
+
+
 def test_solve_host_buffers_and_zero_rhs(tiny):
     L = lib()
     wl = tiny.wl
