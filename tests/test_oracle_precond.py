@@ -63,3 +63,46 @@ def test_pack_roundtrip_and_shapes():
     inter[0::2], inter[1::2] = flat.real, flat.imag
     for a, b in zip(ws, precond.unpack(inter)):
         assert np.array_equal(a, b)
+
+
+def _unit_links(ns, nt):
+    u = np.zeros((nt, ns, ns, ns, 4, 3, 3), dtype=complex)
+    u[...] = np.eye(3)
+    return u
+
+
+def test_free_field_transport_is_a_shift():
+    """Closed form at U = 1: a one-layer network whose only weight is W[1+mu] = 1 moves
+    the field by one site, psi(x+mu), with the antiperiodic sign on the time wrap;
+    W[5+mu] = 1 moves it the other way.  Checked against np.roll."""
+    ns, nt = 2, 4
+    u = _unit_links(ns, nt)
+    psi = synth.random_spinor(ns, nt, seed=8)
+    axis = {0: 3, 1: 2, 2: 1, 3: 0}            # field axes t, z, y, x
+    for mu in range(4):
+        for d, step in ((1 + mu, -1), (5 + mu, 1)):
+            w = np.zeros((9, 1, 1, 4, 4), dtype=complex)
+            w[d, 0, 0] = np.eye(4)
+            got = precond.apply(u, [w], psi)
+            ref = np.roll(psi, step, axis=axis[mu])
+            if mu == 3:                       # hops across the time boundary flip sign
+                if step == -1:
+                    ref[-1] *= -1.0
+                else:
+                    ref[0] *= -1.0
+            assert np.abs(got - ref).max() < 1e-14, (mu, d)
+
+
+def test_scaled_identity_network():
+    """Only W[0] nonzero, alpha_l times the identity in each layer: the network is the
+    product of the alphas times the identity, channels and layers notwithstanding."""
+    u, _ = _setup()
+    alphas = [0.5 + 0.25j, -1.5, 2.0j]
+    ws = []
+    for l, shp in enumerate(precond.layer_shapes(1, 3)):
+        w = np.zeros(shp, dtype=complex)
+        w[0, 0, 0] = alphas[l] * np.eye(4)
+        ws.append(w)
+    psi = synth.random_spinor(2, 4, seed=12)
+    got = precond.apply(u, ws, psi)
+    assert np.abs(got - np.prod(alphas) * psi).max() < 1e-14
