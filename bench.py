@@ -51,6 +51,11 @@ def parse_args(argv=None):
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per solver launch (0: all)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--learned-sample", type=int, default=64, help="sources solved with the learned preconditioner")
+    p.add_argument("--learned-pairs", type=int, default=64, help="(rho, phi) training pairs")
+    p.add_argument("--learned-epochs", type=int, default=8)
+    p.add_argument("--learned-batch", type=int, default=8)
+    p.add_argument("--learned-lr", type=float, default=2e-3)
     p.add_argument("--dslash-sweep", action="store_true", help="print the Dslash GB/s sweep instead of the path step")
     p.add_argument("--dslash-nr", default="1,8,16,32,64", help="right-hand-side counts of the Dslash sweep")
     p.add_argument("--dslash-iters", type=int, default=50, help="solver iterations per sweep point")
@@ -193,6 +198,62 @@ def measured_traffic_ratio(workload):
             if parts[3] == HOP_KERNEL_VERSION and parts[6] == "algorithmic":
                 return float(parts[1]) / float(parts[7])
     return None
+
+
+def learned_leg(L, torch, path, wl, u, rhs, args):
+    """The learned right preconditioner in FGCR(16) on a sample of the step's diluted sources.
+    Training pairs (rho, phi = K^-1 rho): seeded Gaussian rho on the same gauge field, solved by
+    the library to 1e-10; training runs on the GPU with the library's kernels and is reported
+    separately, not in the solve rate.  The sample is then solved with the trained network and
+    with the seeded start network, which shows what training gains."""
+    ctx, lat = path.ctx, path.lat
+    npairs = args.learned_pairs
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4242)
+    shape = (npairs, wl.nt, wl.ns, wl.ns, wl.ns, 4, 3)
+    rho = torch.complex(torch.randn(shape, dtype=torch.float64, device="cuda", generator=gen),
+                        torch.randn(shape, dtype=torch.float64, device="cuda", generator=gen))
+    phi = torch.empty_like(rho)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.dirac_solve_batch(ctx, lat, u, wl.m0, wl.csw, rho, phi, npairs, L.solver_params(mode=L.MIXED_FP32))
+    torch.cuda.synchronize()
+    pairs_s = time.perf_counter() - t0
+    nw = L.laph_precond_size()
+    w0 = np.zeros(nw, dtype=np.float32)
+    L.laph_precond_init(7, wl.m0 + 1.0 + 3.0 / wl.xi, w0)
+    w = w0.copy()
+    adam = np.zeros(2 * nw, dtype=np.float32)
+    grad = torch.empty(nw // 2, dtype=torch.complex128, device="cuda")
+    nb = min(npairs, 16)
+    loss0 = L.laph_precond_grad(ctx, lat, u, wl.m0, wl.csw, w0, rho[:nb], phi[:nb], nb, grad)
+    t0 = time.perf_counter()
+    L.laph_precond_train(ctx, lat, u, wl.m0, wl.csw, rho, phi, npairs, args.learned_epochs, args.learned_batch,
+                         args.learned_lr, 0, w, adam)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    loss1 = L.laph_precond_grad(ctx, lat, u, wl.m0, wl.csw, w, rho[:nb], phi[:nb], nb, grad)
+    del rho, phi
+    n = min(args.learned_sample, rhs.shape[0])
+    sub = rhs[:n].clone()
+    xs = torch.empty_like(sub)
+    out = {"sample": n, "train_pairs": npairs, "train_epochs": args.learned_epochs, "train_batch": args.learned_batch,
+           "pairs_solve_s": pairs_s, "train_s": train_s, "loss_start": loss0, "loss_trained": loss1}
+    stream = torch.cuda.current_stream()
+    for name, ww in (("trained", w), ("start", w0)):
+        wdev = torch.from_numpy(ww).cuda()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        reps = L.dirac_solve_batch(ctx, lat, u, wl.m0, wl.csw, sub, xs, n,
+                                   L.solver_params(mode=L.LEARNED, weights=wdev, rhs_block=n))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"sources_per_s": n / (ev0.elapsed_time(ev1) / 1000.0),
+                     "iters_mean": float(np.mean([r.iters for r in reps])), "iters_max": max(r.iters for r in reps),
+                     "fallback_used": int(sum(r.fallback_used for r in reps)),
+                     "true_resid_max": max(r.true_resid for r in reps)}
+    return out
 
 
 class PathStep:
@@ -381,6 +442,9 @@ def run_ours(args):
         solve_only = nsrc / (ev0.elapsed_time(ev1) / 1000.0)
         variants["mixed_fp32_batched_solve_only"] = {"sources_per_s": solve_only, "rhs_block": min(nsrc, 64),
                                                      "iters_max": max(r.iters for r in sreps)}
+
+    if args.learned_sample > 0 and mode == L.MIXED_FP32:
+        variants["learned_fgcr"] = learned_leg(L, torch, path, wl, u, rhs, args)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",

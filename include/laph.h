@@ -121,7 +121,7 @@ int laph_stout_smear(laph_ctx *ctx, const laph_lattice *lat, void *links, double
  *            order among those within a relative 1e-8 of the largest) is real
  *            and positive.
  *   params   NULL for defaults (lambda_L = 15, lambda_C chosen from a short
- *            Lanczos run, Chebyshev order 8, Krylov dimension
+ *            Lanczos run, Chebyshev order 24, Krylov dimension
  *            max(2 nv + 16, nv + 32), tolerance 1e-11 on ||(-Delta) v - lambda v||
  *            relative to ||-Delta|| <= 12, at most 50 restarts).
  *   report   optional (may be NULL).
@@ -131,7 +131,7 @@ int laph_stout_smear(laph_ctx *ctx, const laph_lattice *lat, void *links, double
 typedef struct {
     double lambda_L;      /* upper bound of the spectrum of -Delta (<= 0: 15)     */
     double lambda_C;      /* cutoff mapped to 1 (<= 0: automatic)                 */
-    int cheb_order;       /* n of T_n (<= 0: 8)                                   */
+    int cheb_order;       /* n of T_n (<= 0: 24)                                  */
     int krylov_dim;       /* Krylov space dimension m (<= 0: automatic)           */
     int max_restarts;     /* (<= 0: 50)                                           */
     double tol;           /* residual tolerance relative to 12 (<= 0: 1e-11)      */

@@ -589,7 +589,7 @@ extern "C" int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *
         laph_eig_params prm{};
         if (params) prm = *params;
         double lamL = prm.lambda_L > 0 ? prm.lambda_L : 15.0;
-        int ncheb = prm.cheb_order > 0 ? prm.cheb_order : 8;
+        int ncheb = prm.cheb_order > 0 ? prm.cheb_order : 24;
         int m = prm.krylov_dim > 0 ? prm.krylov_dim : std::max(2 * nv + 16, nv + 32);
         m = (int)std::min<long>(m, n - 1);
         LAPH_REQUIRE(m > nv, "krylov_dim must exceed nv");

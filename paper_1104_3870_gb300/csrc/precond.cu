@@ -66,12 +66,15 @@ __device__ __forceinline__ void transport12(const float4 *__restrict__ u, bool d
     }
 }
 
-// One layer for all output channels.  Thread (p, cb, r).  Weights staged in shared memory as
-// float4 (re, re, im, im), [9][cout][cin][16].
-__global__ void __launch_bounds__(128) nn_layer_kernel(const int *__restrict__ nbr, const float4 *__restrict__ L,
-                                                       long Vh, int nr, int cin, int cout,
-                                                       const float2 *__restrict__ W, const float2 *__restrict__ in,
-                                                       float2 *__restrict__ out) {
+// One layer for all output channels, weights staged in shared memory as float4 (re, re, im, im),
+// [9][cout][cin][16].  One thread per (site, output channel c, RHS): since W[d][c][c'] acts on
+// spin and T_d on colour and site, out_c = sum_d T_d (sum_{c'} W[d][c][c'] in_{c'}) — each thread
+// mixes the input channels at the source site, then transports the mixed spinor once, with 12
+// accumulators (not 12 cout), so many warps fit on an SM.  Thread index ((p Vh + cb) cout + c) nr + r.
+__global__ void __launch_bounds__(128, 4) nn_layer2_kernel(const int *__restrict__ nbr, const float4 *__restrict__ L,
+                                                        long Vh, int nr, int cin, int cout,
+                                                        const float2 *__restrict__ W, const float2 *__restrict__ in,
+                                                        float2 *__restrict__ out) {
     extern __shared__ float4 wsm[];
     const int nw = 9 * cout * cin * 16;
     for (int i = threadIdx.x; i < nw; i += blockDim.x) {
@@ -79,23 +82,22 @@ __global__ void __launch_bounds__(128) nn_layer_kernel(const int *__restrict__ n
         wsm[i] = make_float4(w.x, w.x, w.y, w.y);
     }
     __syncthreads();
-    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    long site = tid / nr;             // p * Vh + cb
-    int r = (int)(tid - site * nr);
+    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long sc = tid / nr;              // site * cout + c
+    const int r = (int)(tid - sc * nr);
+    const long site = sc / cout;           // p * Vh + cb
+    const int c = (int)(sc - site * cout);
     if (site >= 2 * Vh) return;
-    int p = (int)(site / Vh);
-    long cb = site - (long)p * Vh;
+    const int p = (int)(site / Vh);
+    const long cb = site - (long)p * Vh;
     const long chan = 2 * Vh * 12 * (long)nr;
     const long half = Vh * 12 * (long)nr;
     const int *nb = nbr + site * 8;
-    float2 acc[NN_MAXC][12];
+    float2 acc[12];
 #pragma unroll
-    for (int c = 0; c < NN_MAXC; ++c)
-#pragma unroll
-        for (int k = 0; k < 12; ++k) acc[c][k] = f2(0.f, 0.f);
+    for (int k = 0; k < 12; ++k) acc[k] = f2(0.f, 0.f);
     const long lplane = Vh * 9;
     for (int d = 0; d < 9; ++d) {
-        // source site and transport of direction d
         long src_off;
         const float4 *u = nullptr;
         bool dag = false;
@@ -103,8 +105,8 @@ __global__ void __launch_bounds__(128) nn_layer_kernel(const int *__restrict__ n
         if (d == 0) {
             src_off = (long)p * half + cb * 12 * nr;
         } else {
-            int mu = (d - 1) & 3;
-            bool fwdd = d <= 4;
+            const int mu = (d - 1) & 3;
+            const bool fwdd = d <= 4;
             int j = __ldg(nb + (fwdd ? mu : 4 + mu));
             sgn = j < 0 ? -1.f : 1.f;
             j = j < 0 ? ~j : j;
@@ -112,46 +114,45 @@ __global__ void __launch_bounds__(128) nn_layer_kernel(const int *__restrict__ n
             u = fwdd ? L + ((long)p * 4 + mu) * lplane + cb * 9 : L + ((long)(1 - p) * 4 + mu) * lplane + (long)j * 9;
             dag = !fwdd;
         }
+        float2 y[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) y[k] = f2(0.f, 0.f);
         for (int cp = 0; cp < cin; ++cp) {
-            float2 psi[12], t[12];
-            const float2 *s = in + cp * chan + src_off + r;
+            const float2 *sp = in + cp * chan + src_off + r;
+            const float4 *w = wsm + ((d * cout + c) * cin + cp) * 16;
 #pragma unroll
-            for (int k = 0; k < 12; ++k) psi[k] = s[(long)k * nr];
-            if (d == 0) {
+            for (int si = 0; si < 4; ++si) {
+                float2 ps[3], ip[3];
 #pragma unroll
-                for (int k = 0; k < 12; ++k) t[k] = psi[k];
-            } else {
-                transport12(u, dag, sgn, psi, t);
-            }
-            float2 it[12];
+                for (int col = 0; col < 3; ++col) {
+                    ps[col] = sp[(long)(si * 3 + col) * nr];
+                    ip[col] = ri(ps[col]);
+                }
 #pragma unroll
-            for (int k = 0; k < 12; ++k) it[k] = ri(t[k]);
+                for (int so = 0; so < 4; ++so) {
+                    const float4 e = w[so * 4 + si];
+                    const float2 rr = f2(e.x, e.y), ii = f2(e.z, e.w);
 #pragma unroll
-            for (int c = 0; c < NN_MAXC; ++c) {
-                if (c >= cout) break;
-                const float4 *w = wsm + ((d * cout + c) * cin + cp) * 16;
-#pragma unroll
-                for (int so = 0; so < 4; ++so)
-#pragma unroll
-                    for (int si = 0; si < 4; ++si) {
-                        float4 e = w[so * 4 + si];
-                        float2 rr = f2(e.x, e.y), ii = f2(e.z, e.w);
-#pragma unroll
-                        for (int col = 0; col < 3; ++col) {
-                            acc[c][so * 3 + col] = ffma(rr, t[si * 3 + col], acc[c][so * 3 + col]);
-                            acc[c][so * 3 + col] = ffma(ii, it[si * 3 + col], acc[c][so * 3 + col]);
-                        }
+                    for (int col = 0; col < 3; ++col) {
+                        y[so * 3 + col] = ffma(rr, ps[col], y[so * 3 + col]);
+                        y[so * 3 + col] = ffma(ii, ip[col], y[so * 3 + col]);
                     }
+                }
             }
         }
-    }
+        if (d == 0) {
 #pragma unroll
-    for (int c = 0; c < NN_MAXC; ++c) {
-        if (c >= cout) break;
-        float2 *o = out + c * chan + (long)p * half + cb * 12 * nr + r;
+            for (int k = 0; k < 12; ++k) acc[k] = __fadd2_rn(acc[k], y[k]);
+        } else {
+            float2 t[12];
+            transport12(u, dag, sgn, y, t);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) o[(long)k * nr] = acc[c][k];
+            for (int k = 0; k < 12; ++k) acc[k] = __fadd2_rn(acc[k], t[k]);
+        }
     }
+    float2 *o = out + c * chan + (long)p * half + cb * 12 * nr + r;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[(long)k * nr] = acc[k];
 }
 
 // W'[d][c'][c] = W[dbar][c][c']^dag (adjoint layer: swapped transports, conjugate-transposed spin matrices)
@@ -319,11 +320,11 @@ struct Net {
 
 static void launch_layer(const Net &net, int cin, int cout, const float2 *W, const float2 *in, float2 *out,
                          cudaStream_t s) {
-    long n = 2 * net.Vh * net.nr;
+    long n = 2 * net.Vh * net.nr * cout;
     size_t shm = sizeof(float4) * 9 * cin * cout * 16;
-    if (shm > 48 * 1024) LAPH_CUDA(cudaFuncSetAttribute(nn_layer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    if (shm > 48 * 1024) LAPH_CUDA(cudaFuncSetAttribute(nn_layer2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     prof_begin("nn_layer", s);
-    nn_layer_kernel<<<grid_for(n, 128), 128, shm, s>>>(net.op->nbr, net.op->L32w, net.Vh, net.nr, cin, cout, W, in, out);
+    nn_layer2_kernel<<<grid_for(n, 128), 128, shm, s>>>(net.op->nbr, net.op->L32w, net.Vh, net.nr, cin, cout, W, in, out);
     LAPH_LAUNCH_CHECK();
     prof_end("nn_layer", s, 0.0, 0.0);
 }
@@ -407,11 +408,11 @@ static int fgcr(laph_ctx *ctx, const Net &net, const float2 *W, const float2 *b,
     std::vector<float2 *> acts(net.sh.nlayers + 1);
     for (int l = 0; l <= net.sh.nlayers; ++l)
         acts[l] = (float2 *)ws_get(ctx, "nn:act" + std::to_string(l), sizeof(float2) * full * NN_MAXC);
-    c64 *red = (c64 *)ws_get(ctx, "fgcr:red", sizeof(c64) * 2 * nr);
-    c64 *coef = (c64 *)ws_get(ctx, "fgcr:coef", sizeof(c64) * nr);
+    c64 *red = (c64 *)ws_get(ctx, "fgcr:red", sizeof(c64) * (restart + 2) * nr);
+    c64 *coef = (c64 *)ws_get(ctx, "fgcr:coef", sizeof(c64) * (restart + 1) * nr);
     double *sc = (double *)ws_get(ctx, "fgcr:sc", sizeof(double) * nr);
     RedPlan pl = red_plan(ctx, rows, nr);
-    std::vector<c64> hred(2 * nr), hc(nr);
+    std::vector<c64> hred(2 * nr), hc(nr), hgs;
     std::vector<double> hs(nr), rr0(nr);
     LAPH_CUDA(cudaMemcpyAsync(r, b, sizeof(float2) * full, cudaMemcpyDeviceToDevice, s));
     LAPH_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * full, s));
@@ -449,13 +450,27 @@ static int fgcr(laph_ctx *ctx, const Net &net, const float2 *W, const float2 *b,
             // w_j = K z_j on both parities
             hop_f32(*net.op, 0, HOP_APPLY, (c32 *)Wv[j], (const c32 *)(Z[j] + half), (const c32 *)Z[j], nr, s);
             hop_f32(*net.op, 1, HOP_APPLY, (c32 *)(Wv[j] + half), (const c32 *)Z[j], (const c32 *)(Z[j] + half), nr, s);
-            for (int pass = 0; pass < 2; ++pass)
-                for (int i = 0; i < j; ++i) {
-                    dot(Wv[i], Wv[j]);
-                    for (int k = 0; k < nr; ++k) hc[k] = c64{-hred[k].re, -hred[k].im};
-                    axpy(hc, Wv[i], Wv[j]);
-                    axpy(hc, Z[i], Z[j]);
+            // classical Gram-Schmidt, twice: all j projections of a pass in one round trip
+            for (int pass = 0; pass < 2 && j > 0; ++pass) {
+                for (int i = 0; i < j; i += 3) {
+                    const int m = std::min(3, j - i);
+                    mrhs_dots<float>(ctx, pl, rows, m, (const c32 *)Wv[i], (const c32 *)Wv[j],
+                                     m > 1 ? (const c32 *)Wv[i + 1] : nullptr, m > 1 ? (const c32 *)Wv[j] : nullptr,
+                                     m > 2 ? (const c32 *)Wv[i + 2] : nullptr, m > 2 ? (const c32 *)Wv[j] : nullptr,
+                                     red + (long)i * nr, s);
                 }
+                hgs.resize((size_t)j * nr);
+                LAPH_CUDA(cudaMemcpyAsync(hgs.data(), red, sizeof(c64) * j * nr, cudaMemcpyDeviceToHost, s));
+                LAPH_CUDA(cudaStreamSynchronize(s));
+                for (auto &v : hgs) v = c64{-v.re, -v.im};
+                LAPH_CUDA(cudaMemcpyAsync(coef, hgs.data(), sizeof(c64) * j * nr, cudaMemcpyHostToDevice, s));
+                for (int i = 0; i < j; ++i) {
+                    caxpy_rhs_kernel<<<grid_for(full, 256), 256, 0, s>>>(full, nr, coef + (long)i * nr, Wv[i], Wv[j]);
+                    LAPH_LAUNCH_CHECK();
+                    caxpy_rhs_kernel<<<grid_for(full, 256), 256, 0, s>>>(full, nr, coef + (long)i * nr, Z[i], Z[j]);
+                    LAPH_LAUNCH_CHECK();
+                }
+            }
             dot(Wv[j], Wv[j]);
             for (int k = 0; k < nr; ++k) hs[k] = hred[k].re > 0 ? 1.0 / std::sqrt(hred[k].re) : 0.0;
             LAPH_CUDA(cudaMemcpyAsync(sc, hs.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, s));
