@@ -226,11 +226,11 @@ typedef struct {
     int maxiter;           /* total inner iterations per RHS (<= 0: 100000)        */
     int mode;              /* LAPH_SOLVE_*                                          */
     int rhs_block;         /* RHS per launch (<= 0: autotuned)                     */
-    double inner_tol;      /* inner relative tolerance per cycle (<= 0: 1e-5)      */
+    double inner_tol;      /* inner relative tolerance per cycle (<= 0: 3e-4)      */
     int fallback;          /* 1: finish stalled RHS with the fallback solver        */
     const float *weights;  /* LEARNED only: preconditioner weights (device/host)   */
     int gcr_restart;       /* LEARNED only: FGCR restart length (<= 0: 16)         */
-    int check_every;       /* iterations between host convergence checks (<= 0: 25)*/
+    int check_every;       /* iterations between host convergence checks (<= 0: 5) */
 } laph_solver_params;
 
 typedef struct {

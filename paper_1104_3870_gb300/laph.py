@@ -235,7 +235,7 @@ def laph_make_sources(ctx, lat, evecs, nv, noise_id, config_id, dil, b_list, rhs
 
 
 def solver_params(tol=1e-10, maxiter=100000, mode=MIXED_FP32, rhs_block=0, inner_tol=0.0, fallback=1,
-                  weights=None, gcr_restart=16, check_every=25):
+                  weights=None, gcr_restart=16, check_every=0):
     return SolverParams(tol, maxiter, mode, rhs_block, inner_tol, fallback, _ptr(weights), gcr_restart, check_every)
 
 
