@@ -50,4 +50,14 @@ def rel_err(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
+@functools.lru_cache(maxsize=2)
+def oracle_links(workload):
+    """The oracle's own stout smearing of a workload's seeded field (4D links, 3D links);
+    cached because it takes about a minute at 16^3 x 32."""
+    import synth
+    from oracle import gauge
+    wl = synth.WORKLOADS[workload]
+    return gauge.prepare_links(wl.gauge(), wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
+
+
 requires_gpu = pytest.mark.skipif(not has_gpu(), reason="needs a CUDA GPU")

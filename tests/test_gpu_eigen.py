@@ -12,7 +12,7 @@ import pytest
 
 import synth
 from oracle import gauge, laplacian
-from tests.gpu_util import context, dev, empty, host, lib, requires_gpu
+from tests.gpu_util import context, dev, empty, host, lib, oracle_links, requires_gpu
 
 pytestmark = [pytest.mark.gpu, requires_gpu]
 
@@ -59,7 +59,7 @@ def test_eigvecs_medium_sampled_slices():
     rep = L.laph_eigvecs(context(), lat, dlinks, wl.nv, evals, evecs)
     assert rep.nconv == wl.nv
     # the oracle smears on its own (only the seeded field is shared)
-    _, ut = gauge.prepare_links(u0, wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
+    _, ut = oracle_links("medium_16x32")
     slices = [0, 17, 31]
     sub = ut[slices]
     ev_o, vec_o = laplacian.lowest_eigpairs(sub, wl.nv, "sparse")
