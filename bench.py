@@ -60,6 +60,8 @@ def parse_args(argv=None):
     p.add_argument("--dslash-nr", default="1,8,16,32,64", help="right-hand-side counts of the Dslash sweep")
     p.add_argument("--dslash-iters", type=int, default=50, help="solver iterations per sweep point")
     p.add_argument("--dslash-prec", default="fp32,fp64", help="precisions of the Dslash sweep")
+    p.add_argument("--dslash-direct", action="store_true",
+                   help="time laph_dslash_eo launches alone (clover-inverse mode) instead of inside solver iterations")
     return p.parse_args(argv)
 
 
@@ -494,6 +496,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def dslash_direct_rows(L, torch, path, wl, u, prec, fam, real, hbm, args):
+    """One laph_dslash_eo call per repetition (clover-inverse mode, even output parity) on
+    random half-lattice fields; the library times the hop launch itself with CUDA events.
+    Each call rebuilds the operator first, so the links and clover may still be in L2 when
+    the hop starts (an optimistic figure for small right-hand-side counts)."""
+    vh = wl.ns ** 3 * wl.nt // 2
+    cdt = torch.complex64 if prec == "fp32" else torch.complex128
+    rows = []
+    for nr in [int(v) for v in args.dslash_nr.split(",")]:
+        x = torch.randn((vh, 12, nr), dtype=cdt, device="cuda")
+        out = torch.empty_like(x)
+        times = []
+        by = 0.0
+        for rep in range(max(args.dslash_iters, 1)):
+            L.laph_profile_reset()
+            L.laph_profile_enable(1)
+            L.laph_dslash_eo(path.ctx, path.lat, u, wl.m0, wl.csw, 0, L.HOP_CLOVINV,
+                             L.PREC_FP32 if prec == "fp32" else L.PREC_FP64, x, None, out, nr)
+            torch.cuda.synchronize()
+            L.laph_profile_enable(0)
+            n, ms, by, fl = L.laph_profile_read(fam)
+            times.append(ms / n)
+        med = sorted(times)[len(times) // 2]
+        gbs = by / n / (med / 1000.0) / 1e9
+        rows.append({"precision": prec, "nr": nr, "mode": "clovinv (direct)", "reps": len(times),
+                     "median_launch_us": 1000.0 * med, "algorithmic_bytes_per_launch": by / n, "GBs": gbs,
+                     "frac": gbs / hbm})
+        del x, out
+    return rows
+
+
 def run_dslash_sweep(args):
     """Hop launches inside `--dslash-iters` BiCGStab iterations of a block of nr random
     right-hand sides (the solve stops early, by design, before it converges), averaged
@@ -521,6 +554,9 @@ def run_dslash_sweep(args):
     rows = []
     for prec in args.dslash_prec.split(","):
         mode, fam, real = ((L.MIXED_FP32, "dslash_fp32", 4) if prec == "fp32" else (L.PLAIN_FP64, "dslash_fp64", 8))
+        if args.dslash_direct:
+            rows += dslash_direct_rows(L, torch, path, wl, u, prec, fam, real, hbm, args)
+            continue
         for nr in [int(v) for v in args.dslash_nr.split(",")]:
             b = torch.randn((nr, wl.nt, wl.ns, wl.ns, wl.ns, 4, 3), dtype=torch.complex128, device="cuda")
             x = torch.empty_like(b)

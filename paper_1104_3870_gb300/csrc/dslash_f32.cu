@@ -207,18 +207,24 @@ __global__ void __launch_bounds__(128, MODE == HOP_APPLY ? 6 : 8) hop2_kernel(co
 // refilled with job n+NS as soon as every lane has read it.  Lane 0 issues all copies, so a
 // job costs the warp a handful of instructions, and warps never wait on one another.
 constexpr int HOP3_WARPS = 4;
-constexpr int HOP3_SLOT = 3712;            // 29 x 128 B: 3072 B spinor tile + 144 B link or 576 B clover
-constexpr int HOP3_SPIN = 3072;
+// RPT right-hand sides per lane: a warp owns 32 RPT RHS of its site; the tile of a hop is
+// 12 rows x 256 RPT B, followed by the link (144 B) or the clover block (576 B).
+template <int RPT>
+struct Hop3Geo {
+    static constexpr int SPIN = 3072 * RPT;
+    static constexpr int SLOT = ((SPIN + 576 + 127) / 128) * 128;   // 128-byte aligned slots
+};
 constexpr long long HOP3_WAIT_CYCLES = 1LL << 31;   // about one second at the maximum SM clock
 
 __device__ int g_hop3_timeout;   // set when a copy wait gives up (or the ring is misaligned); read by the host
 
-template <int MODE, int NS>
-__global__ void __launch_bounds__(HOP3_WARPS * 32)
+template <int MODE, int NS, int RPT>
+__global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
     hop3_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_z,
                 const int *__restrict__ nbr, const float4 *__restrict__ L, const float *__restrict__ C, int Vh, int p,
                 float hws, float hwt, float2 *__restrict__ out, int nr, int gshift, int nunits) {
     extern __shared__ __align__(128) unsigned char sm3[];
+    constexpr int HOP3_SPIN = Hop3Geo<RPT>::SPIN, HOP3_SLOT = Hop3Geo<RPT>::SLOT;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (smem_u32(sm3) & 127) {   // tensor copies need 128-byte aligned destinations
         if (threadIdx.x == 0) atomicExch(&g_hop3_timeout, 2);
@@ -254,14 +260,14 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32)
                 const int jn = e < 0 ? ~e : e;
                 meta[islot] = e < 0 ? -w : w;
                 mbar_arrive_expect_tx(b, HOP3_SPIN + 144);
-                tma_tile_2d(sl, &tm_in, 64 * h, 12 * jn, b);
+                tma_tile_2d(sl, &tm_in, 64 * RPT * h, 12 * jn, b);
                 const float4 *u = (ij & 1) ? L + ((long)((1 - p) * 4 + mu) * Vh + jn) * 9
                                            : L + ((long)(p * 4 + mu) * Vh + cb) * 9;
                 bulk_g2s(sl + HOP3_SPIN, u, 144, b);
             } else {
                 constexpr bool needz = MODE != HOP_CLOVINV;
                 mbar_arrive_expect_tx(b, (needz ? HOP3_SPIN : 0) + 576);
-                if (needz) tma_tile_2d(sl, &tm_z, 64 * h, 12 * cb, b);
+                if (needz) tma_tile_2d(sl, &tm_z, 64 * RPT * h, 12 * cb, b);
                 bulk_g2s(sl + HOP3_SPIN, C + ((long)p * Vh + cb) * 144, 576, b);
             }
         }
@@ -295,19 +301,23 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32)
     bool ok = true;
     for (int k = 0, q = gw; k < nu && ok; ++k, q += gstride) {
         const int cb = q >> gshift, h = q & gmask;
-        float2 acc[12];
+        float2 acc[RPT][12];
 #pragma unroll
-        for (int c = 0; c < 12; ++c) acc[c] = ff(0.f, 0.f);
-#define HOP3_DIR(MU, FWD)                                                                                 \
-    if (ok) {                                                                                             \
-        if (!wait()) {                                                                                    \
-            ok = false;                                                                                   \
-        } else {                                                                                          \
-            const unsigned char *sl_ = ring + cslot * HOP3_SLOT;                                          \
-            hop_dir2<MU, FWD, false>(acc, reinterpret_cast<const float2 *>(sl_) + lane, 32,               \
-                                     reinterpret_cast<const float4 *>(sl_ + HOP3_SPIN), meta[cslot]);     \
-            release();                                                                                    \
-        }                                                                                                 \
+        for (int q = 0; q < RPT; ++q)
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[q][c] = ff(0.f, 0.f);
+#define HOP3_DIR(MU, FWD)                                                                                  \
+    if (ok) {                                                                                              \
+        if (!wait()) {                                                                                     \
+            ok = false;                                                                                    \
+        } else {                                                                                           \
+            const unsigned char *sl_ = ring + cslot * HOP3_SLOT;                                           \
+            const float c_ = meta[cslot];                                                                  \
+            _Pragma("unroll") for (int q = 0; q < RPT; ++q)                                                \
+                hop_dir2<MU, FWD, false>(acc[q], reinterpret_cast<const float2 *>(sl_) + 32 * q + lane,    \
+                                         32 * RPT, reinterpret_cast<const float4 *>(sl_ + HOP3_SPIN), c_); \
+            release();                                                                                     \
+        }                                                                                                  \
     }
         HOP3_DIR(0, true)
         HOP3_DIR(0, false)
@@ -324,28 +334,34 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32)
         }
         const unsigned char *sl = ring + cslot * HOP3_SLOT;
         const float *cl = reinterpret_cast<const float *>(sl + HOP3_SPIN);
-        const float2 *zs = reinterpret_cast<const float2 *>(sl) + lane;
-        float2 res[12];
-        if (MODE == HOP_APPLY) {
-            float2 xv[12];
+        float2 res[RPT][12];
 #pragma unroll
-            for (int c = 0; c < 12; ++c) xv[c] = zs[c * 32];
-            herm6_f2<false>(cl, xv, res);
-            herm6_f2<false>(cl + 72, xv + 6, res + 6);
+        for (int q = 0; q < RPT; ++q) {
+            const float2 *zs = reinterpret_cast<const float2 *>(sl) + 32 * q + lane;
+            if (MODE == HOP_APPLY) {
+                float2 xv[12];
 #pragma unroll
-            for (int c = 0; c < 12; ++c) res[c] = add2(res[c], acc[c]);
-        } else {
-            herm6_f2<false>(cl, acc, res);
-            herm6_f2<false>(cl + 72, acc + 6, res + 6);
-            if (MODE == HOP_CLOVINV_XPAY) {
+                for (int c = 0; c < 12; ++c) xv[c] = zs[c * 32 * RPT];
+                herm6_f2<false>(cl, xv, res[q]);
+                herm6_f2<false>(cl + 72, xv + 6, res[q] + 6);
 #pragma unroll
-                for (int c = 0; c < 12; ++c) res[c] = sub2(zs[c * 32], res[c]);
+                for (int c = 0; c < 12; ++c) res[q][c] = add2(res[q][c], acc[q][c]);
+            } else {
+                herm6_f2<false>(cl, acc[q], res[q]);
+                herm6_f2<false>(cl + 72, acc[q] + 6, res[q] + 6);
+                if (MODE == HOP_CLOVINV_XPAY) {
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) res[q][c] = sub2(zs[c * 32 * RPT], res[q][c]);
+                }
             }
         }
         release();
-        float2 *dst = out + (long)cb * 12 * nr + 32 * h + lane;
 #pragma unroll
-        for (int c = 0; c < 12; ++c) dst[(long)c * nr] = res[c];
+        for (int q = 0; q < RPT; ++q) {
+            float2 *dst = out + (long)cb * 12 * nr + 32 * RPT * h + 32 * q + lane;
+#pragma unroll
+            for (int c = 0; c < 12; ++c) dst[(long)c * nr] = res[q][c];
+        }
     }
     if (!ok) {
         if (lane == 0) atomicExch(&g_hop3_timeout, 1);
@@ -361,8 +377,8 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32)
 }
 
 // 2D view of a half-lattice FP32 field [cb][12][nr] complex: rows (cb, component) of 2 nr
-// floats; a box is the 12 rows x 32 right-hand sides that one warp reads.
-static CUtensorMap spinor_map(const float2 *base, long Vh, int nr) {
+// floats; a box is the 12 rows x 32 rpt right-hand sides that one warp reads.
+static CUtensorMap spinor_map(const float2 *base, long Vh, int nr, int rpt) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -374,7 +390,7 @@ static CUtensorMap spinor_map(const float2 *base, long Vh, int nr) {
     CUtensorMap m;
     const cuuint64_t dims[2] = {(cuuint64_t)(2 * nr), (cuuint64_t)(12 * Vh)};
     const cuuint64_t strides[1] = {(cuuint64_t)(2 * nr) * sizeof(float)};
-    const cuuint32_t box[2] = {64, 12};
+    const cuuint32_t box[2] = {(cuuint32_t)(64 * rpt), 12};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -383,58 +399,67 @@ static CUtensorMap spinor_map(const float2 *base, long Vh, int nr) {
     return m;
 }
 
-template <int MODE, int NS>
+template <int MODE, int NS, int RPT>
 static void launch_hop3(const DiracOp &op, int p, float hws, float hwt, float2 *out, const float2 *in,
                         const float2 *z, int nr, cudaStream_t s) {
-    constexpr size_t smem = (size_t)HOP3_WARPS * NS * (HOP3_SLOT + 8 + 4);
+    constexpr size_t smem = (size_t)HOP3_WARPS * NS * (Hop3Geo<RPT>::SLOT + 8 + 4);
     static int bpsm[64] = {0};
     static int nsm[64] = {0};
     int dev = 0;
     LAPH_CUDA(cudaGetDevice(&dev));
     LAPH_REQUIRE(dev < 64, "device index out of range");
     if (bpsm[dev] == 0) {
-        LAPH_CUDA(cudaFuncSetAttribute(hop3_kernel<MODE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        LAPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm[dev], hop3_kernel<MODE, NS>, HOP3_WARPS * 32,
+        LAPH_CUDA(cudaFuncSetAttribute(hop3_kernel<MODE, NS, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LAPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm[dev], hop3_kernel<MODE, NS, RPT>, HOP3_WARPS * 32,
                                                                 smem));
         LAPH_CUDA(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
         LAPH_REQUIRE(bpsm[dev] > 0, "TMA hop kernel does not fit on this device");
     }
     int gshift = 0;
-    while ((32 << gshift) < nr) ++gshift;
-    const CUtensorMap tin = spinor_map(in, op.g.Vh, nr);
-    const CUtensorMap tz = MODE == HOP_CLOVINV ? tin : spinor_map(z, op.g.Vh, nr);
-    const long nunits = op.g.Vh * (nr / 32);
+    while ((32 * RPT << gshift) < nr) ++gshift;
+    const CUtensorMap tin = spinor_map(in, op.g.Vh, nr, RPT);
+    const CUtensorMap tz = MODE == HOP_CLOVINV ? tin : spinor_map(z, op.g.Vh, nr, RPT);
+    const long nunits = op.g.Vh * (nr / (32 * RPT));
     long grid = (nunits + HOP3_WARPS - 1) / HOP3_WARPS;
     const long cap = (long)bpsm[dev] * nsm[dev];
     if (grid > cap) grid = cap;
-    hop3_kernel<MODE, NS><<<(unsigned)grid, HOP3_WARPS * 32, smem, s>>>(
+    hop3_kernel<MODE, NS, RPT><<<(unsigned)grid, HOP3_WARPS * 32, smem, s>>>(
         tin, tz, op.nbr, op.L32w, MODE == HOP_APPLY ? op.C32wA : op.C32w, (int)op.g.Vh, p, hws, hwt, out, nr, gshift,
         (int)nunits);
 }
 
 // Ring depth per warp of the TMA-fed kernel.  Two slots measured fastest on a 16^3 x 32
 // lattice at 32 and 64 right-hand sides: a deeper ring costs more occupancy than its extra
-// prefetch gains.  LAPH_HOP_STAGES = 3, 4 or 6 selects a deeper ring, 0 the register-fed
-// kernel (hop2_kernel) for every shape.
+// prefetch gains.  LAPH_HOP_STAGES = 3 selects a deeper ring, 0 the register-fed kernel
+// (hop2_kernel) for every shape.  LAPH_HOP_RPT = 1 keeps one right-hand side per lane when
+// the block has 64 or more.
 static int hop3_stages() {
     static int ns = -1;
     if (ns < 0) {
         const char *e = getenv("LAPH_HOP_STAGES");
         int v = e ? atoi(e) : 2;
-        ns = (v == 0 || v == 2 || v == 3 || v == 4 || v == 6) ? v : 2;
+        ns = (v == 0 || v == 2 || v == 3) ? v : 2;
     }
     return ns;
 }
+static int hop3_rpt_max() {
+    static int r = -1;
+    if (r < 0) {
+        const char *e = getenv("LAPH_HOP_RPT");
+        r = (e && atoi(e) == 1) ? 1 : 2;
+    }
+    return r;
+}
 
-template <int NS>
+template <int NS, int RPT>
 static void hop3_modes(const DiracOp &op, int p, HopMode mode, float hws, float hwt, float2 *out, const float2 *in,
                        const float2 *z, int nr, cudaStream_t s) {
     if (mode == HOP_APPLY)
-        launch_hop3<HOP_APPLY, NS>(op, p, hws, hwt, out, in, z, nr, s);
+        launch_hop3<HOP_APPLY, NS, RPT>(op, p, hws, hwt, out, in, z, nr, s);
     else if (mode == HOP_CLOVINV)
-        launch_hop3<HOP_CLOVINV, NS>(op, p, hws, hwt, out, in, nullptr, nr, s);
+        launch_hop3<HOP_CLOVINV, NS, RPT>(op, p, hws, hwt, out, in, nullptr, nr, s);
     else
-        launch_hop3<HOP_CLOVINV_XPAY, NS>(op, p, hws, hwt, out, in, z, nr, s);
+        launch_hop3<HOP_CLOVINV_XPAY, NS, RPT>(op, p, hws, hwt, out, in, z, nr, s);
 }
 
 void hop_timeout_check() {
@@ -466,12 +491,13 @@ void hop_f32(const DiracOp &op, int p, HopMode mode, c32 *out, const c32 *in, co
     if (pow2 && aligned && ns > 0 && op.g.Vh * (nr / 32) < (1L << 30)) {
         float2 *o = (float2 *)out;
         const float2 *i = (const float2 *)in, *zz = (const float2 *)z;
-        switch (ns) {
-            case 3: hop3_modes<3>(op, p, mode, hws, hwt, o, i, zz, nr, s); break;
-            case 6: hop3_modes<6>(op, p, mode, hws, hwt, o, i, zz, nr, s); break;
-            case 4: hop3_modes<4>(op, p, mode, hws, hwt, o, i, zz, nr, s); break;
-            default: hop3_modes<2>(op, p, mode, hws, hwt, o, i, zz, nr, s); break;
-        }
+        const bool two = hop3_rpt_max() == 2 && nr % 64 == 0;
+        if (ns == 3)
+            two ? hop3_modes<3, 2>(op, p, mode, hws, hwt, o, i, zz, nr, s)
+                : hop3_modes<3, 1>(op, p, mode, hws, hwt, o, i, zz, nr, s);
+        else
+            two ? hop3_modes<2, 2>(op, p, mode, hws, hwt, o, i, zz, nr, s)
+                : hop3_modes<2, 1>(op, p, mode, hws, hwt, o, i, zz, nr, s);
     } else if (mode == HOP_APPLY)
         hop2_kernel<HOP_APPLY><<<grid, block, 0, s>>>(op.nbr, op.L32w, op.C32wA, op.g.Vh, p, hws, hwt, (float2 *)out,
                                                       (const float2 *)in, (const float2 *)z, nr);
