@@ -181,7 +181,7 @@ def oracle_sample(wl, seconds=15.0, threads=None):
 
 
 # ----------------------------------------------------------------------------- ncu traffic record
-HOP_KERNEL_VERSION = "hop3_tma_ns2"
+HOP_KERNEL_VERSION = "hop3_tma_ns2_rpt2"
 
 
 def measured_traffic_ratio(workload):
