@@ -56,6 +56,12 @@ def parse_args(argv=None):
     p.add_argument("--learned-epochs", type=int, default=8)
     p.add_argument("--learned-batch", type=int, default=8)
     p.add_argument("--learned-lr", type=float, default=2e-3)
+    p.add_argument("--learned-study", action="store_true",
+                   help="print the held-out-field study of the learned preconditioner instead of the path step")
+    p.add_argument("--study-fields", type=int, default=20, help="seeded fields (the last 4 held out)")
+    p.add_argument("--study-pairs", type=int, default=16, help="training pairs per training field")
+    p.add_argument("--study-epochs", type=int, default=4, help="passes over all training fields")
+    p.add_argument("--study-rhs", type=int, default=16, help="sources solved per held-out field")
     p.add_argument("--dslash-sweep", action="store_true", help="print the Dslash GB/s sweep instead of the path step")
     p.add_argument("--dslash-nr", default="1,8,16,32,64", help="right-hand-side counts of the Dslash sweep")
     p.add_argument("--dslash-iters", type=int, default=50, help="solver iterations per sweep point")
@@ -583,9 +589,111 @@ def run_dslash_sweep(args):
                       "rows": rows}), flush=True)
 
 
+def run_learned_study(args):
+    """Learned preconditioner across gauge fields: fields are seeded 2000 + i on the medium
+    lattice (the workload's smearing recipe and m0); the network is trained on (rho, phi =
+    K^-1 rho) pairs of all but the last four fields (Adam state carried across fields, one
+    epoch per field per pass), then on each held-out field the same seeded sources are solved
+    with learned FGCR(16) (batched, FP32 inner, FP64 outer) and with plain FP64 BiCGStab (one
+    right-hand side per launch) and with the mixed batched BiCGStab; iterations and wall time
+    are reported per field."""
+    import torch
+    from paper_1104_3870_gb300 import build
+    build.build()
+    from paper_1104_3870_gb300 import laph as L
+    from paper_1104_3870_gb300.pipeline import LapHPath, LatticeSpec
+    import synth
+
+    wl = synth.WORKLOADS[args.workload]
+    spec = LatticeSpec(wl.ns, wl.nt, wl.xi, wl.m0, wl.csw, wl.nv, (wl.dil_time, wl.dil_spin, wl.dil_laph),
+                       wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
+    path = LapHPath(spec, 0)
+    ctx, lat = path.ctx, path.lat
+    nf, held = args.study_fields, 4
+    shape = lambda n: (n, wl.nt, wl.ns, wl.ns, wl.ns, 4, 3)
+    gen = torch.Generator(device="cuda")
+    nw = L.laph_precond_size()
+    w = np.zeros(nw, dtype=np.float32)
+    L.laph_precond_init(7, wl.m0 + 1.0 + 3.0 / wl.xi, w)
+    adam = np.zeros(2 * nw, dtype=np.float32)
+    step = 0
+    t_pairs = t_train = 0.0
+    train = []
+    for f in range(nf - held):
+        u, _ = path.prepare_links(synth.random_su3_field(wl.ns, wl.nt, seed=2000 + f))
+        gen.manual_seed(7000 + f)
+        rho = torch.complex(torch.randn(shape(args.study_pairs), dtype=torch.float64, device="cuda", generator=gen),
+                            torch.randn(shape(args.study_pairs), dtype=torch.float64, device="cuda", generator=gen))
+        phi = torch.empty_like(rho)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        L.dirac_solve_batch(ctx, lat, u, wl.m0, wl.csw, rho, phi, args.study_pairs, L.solver_params(mode=L.MIXED_FP32))
+        torch.cuda.synchronize()
+        t_pairs += time.perf_counter() - t
+        train.append((u, rho, phi))
+    batch = min(8, args.study_pairs)
+    losses = []
+    for ep in range(args.study_epochs):
+        tot = 0.0
+        for (u, rho, phi) in train:
+            t = time.perf_counter()
+            tot += L.laph_precond_train(ctx, lat, u, wl.m0, wl.csw, rho, phi, args.study_pairs, 1, batch, 2e-3, step,
+                                        w, adam)
+            torch.cuda.synchronize()
+            t_train += time.perf_counter() - t
+            step += args.study_pairs // batch
+        losses.append(tot / len(train))
+    del train
+    wdev = torch.from_numpy(w).cuda()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0, reps
+
+    fields = []
+    n = args.study_rhs
+    for f in range(nf - held, nf):
+        u, _ = path.prepare_links(synth.random_su3_field(wl.ns, wl.nt, seed=2000 + f))
+        gen.manual_seed(9000 + f)
+        b = torch.complex(torch.randn(shape(n), dtype=torch.float64, device="cuda", generator=gen),
+                          torch.randn(shape(n), dtype=torch.float64, device="cuda", generator=gen))
+        x = torch.empty_like(b)
+        row = {"seed": 2000 + f}
+        for name, prm in (("learned_fgcr", L.solver_params(mode=L.LEARNED, weights=wdev, rhs_block=n)),
+                          ("plain_fp64_bicgstab", L.solver_params(mode=L.PLAIN_FP64, rhs_block=1)),
+                          ("mixed_bicgstab", L.solver_params(mode=L.MIXED_FP32, rhs_block=n))):
+            sec, reps = timed(lambda: L.dirac_solve_batch(ctx, lat, u, wl.m0, wl.csw, b, x, n, prm))
+            row[name] = {"s": sec, "sources_per_s": n / sec, "iters_mean": float(np.mean([r.iters for r in reps])),
+                         "true_resid_max": max(r.true_resid for r in reps),
+                         "fallback_used": int(sum(r.fallback_used for r in reps))}
+        fields.append(row)
+    agg = {k: {"sources_per_s": float(np.mean([r[k]["sources_per_s"] for r in fields])),
+               "iters_mean": float(np.mean([r[k]["iters_mean"] for r in fields]))}
+           for k in ("learned_fgcr", "plain_fp64_bicgstab", "mixed_bicgstab")}
+    print(json.dumps({"metric": "learned preconditioner on held-out fields (diluted-source solves to 1e-10)",
+                      "workload": f"{wl.name} lattice, fields seeded 2000..{2000 + nf - 1}, last {held} held out",
+                      "train": {"fields": nf - held, "pairs_per_field": args.study_pairs, "epochs": args.study_epochs,
+                                "batch": batch, "lr": 2e-3, "pairs_solve_s": t_pairs, "train_s": t_train,
+                                "loss_per_epoch": losses},
+                      "held_out": fields, "mean": agg,
+                      "iteration_ratio_learned_vs_plain": agg["learned_fgcr"]["iters_mean"] /
+                      agg["plain_fp64_bicgstab"]["iters_mean"],
+                      "wall_ratio_learned_vs_plain": agg["plain_fp64_bicgstab"]["sources_per_s"] /
+                      agg["learned_fgcr"]["sources_per_s"]}), flush=True)
+    path.close()
+
+
 def main(argv=None):
     args = parse_args(argv)
-    if args.dslash_sweep:
+    if args.learned_study:
+        run_learned_study(args)
+    elif args.dslash_sweep:
         run_dslash_sweep(args)
     elif args.impl == "reference":
         run_reference(args)
