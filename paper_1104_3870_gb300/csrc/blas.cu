@@ -76,6 +76,11 @@ static void run_reduce(laph_ctx *ctx, const RedPlan &pl, long nrows, const Body 
     prof_end(fam, s, 0.0, 0.0);
 }
 
+void red_final_sum(const c64 *partial, int nblk, int nred, int nr, c64 *out, cudaStream_t s) {
+    red_final<<<nred * nr, 256, 0, s>>>(partial, nblk, nred, nr, out);
+    LAPH_LAUNCH_CHECK();
+}
+
 template <typename T>
 struct Dots1 {
     using Acc = cpx<T>;

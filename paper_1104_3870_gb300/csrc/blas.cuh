@@ -22,6 +22,9 @@ template <typename T>
 void mrhs_dots(laph_ctx *ctx, const RedPlan &pl, long nrows, int nred, const cpx<T> *a0, const cpx<T> *b0,
                const cpx<T> *a1, const cpx<T> *b1, const cpx<T> *a2, const cpx<T> *b2, c64 *out, cudaStream_t s);
 
+// out[k][r] = sum over blocks b of partial[b][k][r], in a fixed order (FP64).
+void red_final_sum(const c64 *partial, int nblk, int nred, int nr, c64 *out, cudaStream_t s);
+
 // y[row][r] = y + scale[r] * x   (x of type Tx, y of type Ty)
 template <typename Tx, typename Ty>
 void mrhs_axpy_scaled(long nrows, int nr, const double *scale, const cpx<Tx> *x, cpx<Ty> *y, cudaStream_t s);

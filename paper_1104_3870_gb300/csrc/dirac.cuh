@@ -63,6 +63,11 @@ void hop(const DiracOp &op, int p, HopMode mode, cpx<T> *out, const cpx<T> *in, 
 void hop_timeout_check();
 void hop_f32(const DiracOp &op, int p, HopMode mode, cpx<float> *out, const cpx<float> *in, const cpx<float> *z,
              int nr, cudaStream_t s);
+// The xpay hop out = z - A_pp^{-1} D in with the inner products <out, z> and <out, out> of every
+// right-hand side fused into its epilogue: red[0][r] = <out, z>, red[1][r] = <out, out>.
+// Returns false (launching nothing) where the fused form is not available for this shape.
+bool hop_f32_xpay_dots(laph_ctx *ctx, const DiracOp &op, int p, cpx<float> *out, const cpx<float> *in,
+                       const cpx<float> *z, int nr, cpx<double> *red, cudaStream_t s);
 
 // BF16-stored inner operator: spinors, links and clover inverse in BF16, FP32 arithmetic.
 void hop_bf16(const DiracOp &op, int p, HopMode mode, __nv_bfloat162 *out, const __nv_bfloat162 *in,

@@ -20,6 +20,7 @@
 
 #include <cstdlib>
 
+#include "blas.cuh"
 #include "dirac.cuh"
 #include "tma.cuh"
 
@@ -218,11 +219,15 @@ constexpr long long HOP3_WAIT_CYCLES = 1LL << 31;   // about one second at the m
 
 __device__ int g_hop3_timeout;   // set when a copy wait gives up (or the ring is misaligned); read by the host
 
-template <int MODE, int NS, int RPT>
+// DOTS (xpay mode, nr = 32 RPT): the epilogue also accumulates, per right-hand side, the inner
+// products <out, z> and <out, out> of the warp's sites in FP32 and writes them as the warp's
+// partial sums partial[warp][k][r] (k = 0, 1; FP64) for a fixed-order final sum.
+template <int MODE, int NS, int RPT, bool DOTS = false>
 __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
     hop3_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_z,
                 const int *__restrict__ nbr, const float4 *__restrict__ L, const float *__restrict__ C, int Vh, int p,
-                float hws, float hwt, float2 *__restrict__ out, int nr, int gshift, int nunits) {
+                float hws, float hwt, float2 *__restrict__ out, int nr, int gshift, int nunits,
+                c64 *__restrict__ partial) {
     extern __shared__ __align__(128) unsigned char sm3[];
     constexpr int HOP3_SPIN = Hop3Geo<RPT>::SPIN, HOP3_SLOT = Hop3Geo<RPT>::SLOT;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -302,6 +307,13 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
     };
 
     for (int k = 0; k < NS; ++k) issue();
+    float2 dts[RPT];
+    float dtt[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        dts[q] = ff(0.f, 0.f);
+        dtt[q] = 0.f;
+    }
     bool ok = true;
     for (int k = 0, q = gw; k < nu && ok; ++k, q += gstride) {
         const int cb = q >> gshift, h = q & gmask;
@@ -355,7 +367,16 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
                 herm6_f2<false>(cl + 72, acc[q] + 6, res[q] + 6);
                 if (MODE == HOP_CLOVINV_XPAY) {
 #pragma unroll
-                    for (int c = 0; c < 12; ++c) res[q][c] = sub2(zs[c * 32 * RPT], res[q][c]);
+                    for (int c = 0; c < 12; ++c) {
+                        const float2 zc = zs[c * 32 * RPT];
+                        res[q][c] = sub2(zc, res[q][c]);
+                        if (DOTS) {   // conj(t) z and |t|^2
+                            const float2 t = res[q][c];
+                            dts[q].x = fmaf(t.x, zc.x, fmaf(t.y, zc.y, dts[q].x));
+                            dts[q].y = fmaf(t.x, zc.y, fmaf(-t.y, zc.x, dts[q].y));
+                            dtt[q] = fmaf(t.x, t.x, fmaf(t.y, t.y, dtt[q]));
+                        }
+                    }
                 }
             }
         }
@@ -365,6 +386,15 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
             float2 *dst = out + (long)cb * 12 * nr + 32 * RPT * h + 32 * q + lane;
 #pragma unroll
             for (int c = 0; c < 12; ++c) dst[(long)c * nr] = res[q][c];
+        }
+    }
+    if (DOTS) {   // every warp writes, zeros where it had no units
+        const int gwarp = blockIdx.x * HOP3_WARPS + warp;
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int r = 32 * q + lane;
+            partial[((long)gwarp * 2 + 0) * nr + r] = c64{(double)dts[q].x, (double)dts[q].y};
+            partial[((long)gwarp * 2 + 1) * nr + r] = c64{(double)dtt[q], 0.0};
         }
     }
     if (!ok) {
@@ -403,9 +433,9 @@ static CUtensorMap spinor_map(const float2 *base, long Vh, int nr, int rpt) {
     return m;
 }
 
-template <int MODE, int NS, int RPT>
-static void launch_hop3(const DiracOp &op, int p, float hws, float hwt, float2 *out, const float2 *in,
-                        const float2 *z, int nr, cudaStream_t s) {
+template <int MODE, int NS, int RPT, bool DOTS = false>
+static long launch_hop3(const DiracOp &op, int p, float hws, float hwt, float2 *out, const float2 *in,
+                        const float2 *z, int nr, cudaStream_t s, laph_ctx *ctx = nullptr, c64 *red = nullptr) {
     constexpr size_t smem = (size_t)HOP3_WARPS * NS * (Hop3Geo<RPT>::SLOT + 8 + 4);
     static int bpsm[64] = {0};
     static int nsm[64] = {0};
@@ -413,9 +443,10 @@ static void launch_hop3(const DiracOp &op, int p, float hws, float hwt, float2 *
     LAPH_CUDA(cudaGetDevice(&dev));
     LAPH_REQUIRE(dev < 64, "device index out of range");
     if (bpsm[dev] == 0) {
-        LAPH_CUDA(cudaFuncSetAttribute(hop3_kernel<MODE, NS, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        LAPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm[dev], hop3_kernel<MODE, NS, RPT>, HOP3_WARPS * 32,
-                                                                smem));
+        LAPH_CUDA(cudaFuncSetAttribute(hop3_kernel<MODE, NS, RPT, DOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+        LAPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm[dev], hop3_kernel<MODE, NS, RPT, DOTS>,
+                                                                HOP3_WARPS * 32, smem));
         LAPH_CUDA(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
         LAPH_REQUIRE(bpsm[dev] > 0, "TMA hop kernel does not fit on this device");
     }
@@ -427,9 +458,16 @@ static void launch_hop3(const DiracOp &op, int p, float hws, float hwt, float2 *
     long grid = (nunits + HOP3_WARPS - 1) / HOP3_WARPS;
     const long cap = (long)bpsm[dev] * nsm[dev];
     if (grid > cap) grid = cap;
-    hop3_kernel<MODE, NS, RPT><<<(unsigned)grid, HOP3_WARPS * 32, smem, s>>>(
+    c64 *partial = nullptr;
+    if (DOTS) partial = (c64 *)ws_get(ctx, "hop3:dots", sizeof(c64) * 2 * nr * grid * HOP3_WARPS);
+    hop3_kernel<MODE, NS, RPT, DOTS><<<(unsigned)grid, HOP3_WARPS * 32, smem, s>>>(
         tin, tz, op.nbr, op.L32w, MODE == HOP_APPLY ? op.C32wA : op.C32w, (int)op.g.Vh, p, hws, hwt, out, nr, gshift,
-        (int)nunits);
+        (int)nunits, partial);
+    if (DOTS) {
+        LAPH_LAUNCH_CHECK();
+        red_final_sum(partial, (int)(grid * HOP3_WARPS), 2, nr, red, s);
+    }
+    return grid * HOP3_WARPS;
 }
 
 // Ring depth per warp of the TMA-fed kernel.  Two slots measured fastest on a 16^3 x 32
@@ -513,6 +551,26 @@ void hop_f32(const DiracOp &op, int p, HopMode mode, c32 *out, const c32 *in, co
                                                              (float2 *)out, (const float2 *)in, (const float2 *)z, nr);
     LAPH_LAUNCH_CHECK();
     prof_end("dslash_fp32", s, hop_bytes(op, mode, nr, sizeof(float)), hop_flops(op, nr));
+}
+
+bool hop_f32_xpay_dots(laph_ctx *ctx, const DiracOp &op, int p, c32 *out, const c32 *in, const c32 *z, int nr,
+                       c64 *red, cudaStream_t s) {
+    const bool aligned = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(z) |
+                           reinterpret_cast<uintptr_t>(op.L32w) | reinterpret_cast<uintptr_t>(op.C32w)) & 15) == 0;
+    const int ns = hop3_stages();
+    const int rpt = (hop3_rpt_max() == 2 && nr == 64) ? 2 : 1;
+    if (!aligned || ns != 2 || nr != 32 * rpt) return false;
+    float hws = (float)op.hw[0], hwt = (float)op.hw[3];
+    prof_begin("dslash_fp32", s);
+    if (rpt == 2)
+        launch_hop3<HOP_CLOVINV_XPAY, 2, 2, true>(op, p, hws, hwt, (float2 *)out, (const float2 *)in,
+                                                  (const float2 *)z, nr, s, ctx, red);
+    else
+        launch_hop3<HOP_CLOVINV_XPAY, 2, 1, true>(op, p, hws, hwt, (float2 *)out, (const float2 *)in,
+                                                  (const float2 *)z, nr, s, ctx, red);
+    LAPH_LAUNCH_CHECK();
+    prof_end("dslash_fp32", s, hop_bytes(op, HOP_CLOVINV_XPAY, nr, sizeof(float)), hop_flops(op, nr));
+    return true;
 }
 
 // ------------------------------------------------------------------ operand preparation

@@ -9,6 +9,7 @@
 // the full operator.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "blas.cuh"
@@ -28,6 +29,19 @@ template <typename T>
 static void schur_apply(const DiracOp &op, int nr, const cpx<T> *in, cpx<T> *out, cpx<T> *tmp_o, cudaStream_t s) {
     hop<T>(op, 1, HOP_CLOVINV, tmp_o, in, nullptr, nullptr, nr, s);          // tmp = A_oo^{-1} D_oe in
     hop<T>(op, 0, HOP_CLOVINV_XPAY, out, tmp_o, in, nullptr, nr, s);        // out = in - A_ee^{-1} D_eo tmp
+}
+
+// t = M s and the two inner products <t, s>, <t, t> into red[0..1][r]; in FP32 the products
+// come out of the epilogue of the second hop where that form exists.
+template <typename T>
+static void schur_apply_tdots(laph_ctx *ctx, const RedPlan &pl, long nrows, const DiracOp &op, int nr,
+                              const cpx<T> *sv, cpx<T> *t, cpx<T> *tmp_o, c64 *red, cudaStream_t s) {
+    hop<T>(op, 1, HOP_CLOVINV, tmp_o, sv, nullptr, nullptr, nr, s);
+    if (std::is_same<T, float>::value &&
+        hop_f32_xpay_dots(ctx, op, 0, (c32 *)t, (const c32 *)tmp_o, (const c32 *)sv, nr, red, s))
+        return;
+    hop<T>(op, 0, HOP_CLOVINV_XPAY, t, tmp_o, sv, nullptr, nr, s);
+    mrhs_dots<T>(ctx, pl, nrows, 2, t, sv, t, t, nullptr, nullptr, red, s);
 }
 
 // BiCGStab on the Schur operator for nr right-hand sides at once, x = 0 start.
@@ -73,8 +87,7 @@ static InnerStats bicgstab_schur(laph_ctx *ctx, const DiracOp &op, int nr, const
         mrhs_dots<T>(ctx, pl, nrows, 1, rh, v, nullptr, nullptr, nullptr, nullptr, red, s);
         bicg_alpha(nr, sc, red, s);
         bicg_s_update<T>(nrows, nr, sc, r, v, sv, s);
-        schur_apply<T>(op, nr, sv, t, tmp, s);
-        mrhs_dots<T>(ctx, pl, nrows, 2, t, sv, t, t, nullptr, nullptr, red, s);
+        schur_apply_tdots<T>(ctx, pl, nrows, op, nr, sv, t, tmp, red, s);
         bicg_omega(nr, sc, red, s);
         bicg_xr_update_reduce<T>(ctx, pl, nrows, sc, x, p, sv, t, r, rh, red, s);
         bicg_rho(nr, sc, red, s);
