@@ -448,7 +448,11 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         solve_only = nsrc / (ev0.elapsed_time(ev1) / 1000.0)
-        variants["mixed_fp32_batched_solve_only"] = {"sources_per_s": solve_only, "rhs_block": min(nsrc, 64),
+        vh = wl.ns ** 3 * wl.nt // 2
+        tuned = max([L.laph_tuned_block(path.ctx, vh, c) for c in (16, 32, 64, 128)])
+        variants["mixed_fp32_batched_solve_only"] = {"sources_per_s": solve_only,
+                                                     "rhs_block": (args.rhs_block or tuned),
+                                                     "rhs_block_source": "argument" if args.rhs_block else "autotuned",
                                                      "iters_max": max(r.iters for r in sreps)}
 
     if args.learned_sample > 0 and mode == L.MIXED_FP32:

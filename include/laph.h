@@ -225,7 +225,8 @@ typedef struct {
     double tol;            /* FP64 true relative residual target (<= 0: 1e-10)     */
     int maxiter;           /* total inner iterations per RHS (<= 0: 100000)        */
     int mode;              /* LAPH_SOLVE_*                                          */
-    int rhs_block;         /* RHS per launch (<= 0: autotuned)                     */
+    int rhs_block;         /* RHS per launch (<= 0: PLAIN 1, LEARNED min(nrhs, 64),
+                              MIXED autotuned, see laph_tuned_block)                */
     double inner_tol;      /* inner relative tolerance per cycle (<= 0: 3e-4)      */
     int fallback;          /* 1: finish stalled RHS with the fallback solver        */
     const float *weights;  /* LEARNED only: preconditioner weights (device/host)   */
@@ -244,6 +245,13 @@ typedef struct {
 int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const void *links,
                       const laph_dirac_params *dirac, const void *rhs, void *sol, int nrhs,
                       const laph_solver_params *params, laph_solve_report *report, void *stream);
+
+/* RHS block the mixed solver's autotuner chose for a lattice of vh = V/2 sites, where nmax is
+ * the largest candidate block that fitted (16, 32, 64 or 128, at most nrhs); 0 if no mixed
+ * solve with rhs_block <= 0 has needed it in this context yet.  The tuner times the FP32
+ * Schur operator and one reduction at each candidate on scratch fields once and keeps the
+ * block with the lowest time per right-hand side (ties within 3 % go to the larger block). */
+int laph_tuned_block(laph_ctx *ctx, int vh, int nmax);
 
 /* ------------------------------------------------------------------------
  * Learned preconditioner for LAPH_SOLVE_LEARNED (the paper has no learned

@@ -303,9 +303,70 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
     }
 }
 
+// RHS block of the mixed solver when the caller leaves the choice to the library: among the
+// block sizes 16, 32, 64 and 128 that do not exceed nrhs and whose solver vectors fit in 60 % of
+// the free device memory, the one with the lowest time per right-hand side of one inner
+// iteration's operator work (the Schur operator, then one two-product reduction), measured
+// with CUDA events on scratch fields once per lattice size and candidate set and cached in
+// the context.
+static int autotune_block(laph_ctx *ctx, const DiracOp &op, int nrhs, cudaStream_t s) {
+    if (nrhs <= 16) return nrhs;
+    const long nrows = op.g.Vh * 12;
+    size_t free_b = 0, total_b = 0;
+    LAPH_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const double per_rhs = (double)nrows * (10 * sizeof(c64) + 10 * sizeof(c32));   // FP64 outer + FP32 inner vectors
+    std::vector<int> cand;
+    for (int c : {16, 32, 64, 128})
+        if (c <= nrhs && c * per_rhs <= 0.6 * (double)free_b) cand.push_back(c);
+    if (cand.empty()) return 16;
+    const std::string key = "mixed_block:" + std::to_string(op.g.Vh) + ":" + std::to_string(cand.back());
+    auto it = ctx->tune.find(key);
+    if (it != ctx->tune.end()) return it->second;
+    const int nmax = cand.back();
+    c32 *a = (c32 *)ws_get(ctx, "tune:a", sizeof(c32) * nrows * nmax);
+    c32 *b = (c32 *)ws_get(ctx, "tune:b", sizeof(c32) * nrows * nmax);
+    c32 *t = (c32 *)ws_get(ctx, "tune:t", sizeof(c32) * nrows * nmax);
+    c64 *red = (c64 *)ws_get(ctx, "tune:red", sizeof(c64) * 2 * nmax);
+    LAPH_CUDA(cudaMemsetAsync(a, 0, sizeof(c32) * nrows * nmax, s));
+    cudaEvent_t e0, e1;
+    LAPH_CUDA(cudaEventCreate(&e0));
+    LAPH_CUDA(cudaEventCreate(&e1));
+    int best = cand.back();
+    double best_t = 1e300;
+    for (int nr : cand) {
+        RedPlan pl = red_plan(ctx, nrows, nr);
+        auto once = [&]() {
+            schur_apply<float>(op, nr, a, b, t, s);
+            mrhs_dots<float>(ctx, pl, nrows, 2, b, a, b, b, nullptr, nullptr, red, s);
+        };
+        once();
+        LAPH_CUDA(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 3; ++rep) once();
+        LAPH_CUDA(cudaEventRecord(e1, s));
+        LAPH_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        LAPH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const double per = ms / (3.0 * nr);
+        if (per < best_t * 0.97 || (per <= best_t * 1.03 && nr > best)) {   // ties go to the larger block
+            best_t = std::min(per, best_t);
+            best = nr;
+        }
+    }
+    LAPH_CUDA(cudaEventDestroy(e0));
+    LAPH_CUDA(cudaEventDestroy(e1));
+    ctx->tune[key] = best;
+    return best;
+}
+
 }  // namespace laph
 
 using namespace laph;
+
+extern "C" int laph_tuned_block(laph_ctx *ctx, int vh, int nmax) {
+    if (!ctx) return 0;
+    auto it = ctx->tune.find("mixed_block:" + std::to_string(vh) + ":" + std::to_string(nmax));
+    return it == ctx->tune.end() ? 0 : it->second;
+}
 
 extern "C" int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const void *links,
                                  const laph_dirac_params *dirac, const void *rhs, void *sol, int nrhs,
@@ -338,7 +399,10 @@ extern "C" int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const v
         if (prm.mode == LAPH_SOLVE_LEARNED)
             wdev = (const float *)stage_in(ctx, prm.weights, sizeof(float) * laph_precond_size(), "learned_w", s);
         int blk = prm.rhs_block;
-        if (blk <= 0) blk = prm.mode == LAPH_SOLVE_PLAIN_FP64 ? 1 : std::min(nrhs, 64);
+        if (blk <= 0)
+            blk = prm.mode == LAPH_SOLVE_PLAIN_FP64 ? 1
+                  : prm.mode == LAPH_SOLVE_MIXED_FP32 ? autotune_block(ctx, op, nrhs, s)
+                                                      : std::min(nrhs, 64);
         blk = std::min(blk, std::min(nrhs, 256));
         std::vector<laph_solve_report> rep(nrhs);
         for (int first = 0; first < nrhs; first += blk) {

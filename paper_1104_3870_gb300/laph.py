@@ -91,6 +91,7 @@ _sig = {
                                          ctypes.c_int, ctypes.POINTER(SolverParams), _vp, _vp]),
     "laph_dirac_apply": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), _vp, _vp,
                                         ctypes.c_int, _vp]),
+    "laph_tuned_block": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "laph_dslash_eo": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "laph_sinks": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
@@ -251,6 +252,10 @@ def dirac_solve_batch(ctx, lat, links, m0, csw, rhs, sol, nrhs, params=None, str
 def laph_dirac_apply(ctx, lat, links, m0, csw, inp, out, nrhs, stream=None):
     _check(_lib.laph_dirac_apply(ctx.ptr, ctypes.byref(lat), _ptr(links), ctypes.byref(DiracParams(m0, csw)),
                                  _ptr(inp), _ptr(out), int(nrhs), _stream(stream)))
+
+
+def laph_tuned_block(ctx, vh, nmax):
+    return int(_lib.laph_tuned_block(ctx.ptr, int(vh), int(nmax)))
 
 
 def laph_dslash_eo(ctx, lat, links, m0, csw, parity, mode, precision, inp, z, out, nrhs, stream=None):

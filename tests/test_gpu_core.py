@@ -225,3 +225,28 @@ def test_correlators_partial_dilution_same_noise(tiny, channel):
         tiny.dil = saved
     ref = olaph.pipi_i2(*ol, t0) if channel == "pipi" else olaph.meson_connected(ol[0], ol[1], t0, "pion")
     assert corr_close(host(corr), ref, 1e-8)
+
+
+def test_empty_inputs(tiny):
+    """Zero right-hand sides or projectors are valid calls that write nothing; zero-sized
+    correlator inputs and hops are rejected as argument errors."""
+    import torch
+    L = lib()
+    wl = tiny.wl
+    lat = L.lattice(wl.ns, wl.nt, wl.xi)
+    u = dev(tiny.u)
+    sentinel = torch.full((1, wl.nt, wl.ns, wl.ns, wl.ns, 4, 3), 7.0 + 7.0j, dtype=torch.complex128, device="cuda")
+    reps = L.dirac_solve_batch(context(), lat, u, wl.m0, wl.csw, sentinel, sentinel, 0, L.solver_params())
+    assert reps == [] and bool((sentinel == 7.0 + 7.0j).all())
+    evecs = dev(tiny.evecs)
+    coef = torch.full((1, wl.nt, 4, wl.nv), 7.0, dtype=torch.complex128, device="cuda")
+    L.laph_sinks(context(), lat, evecs, wl.nv, sentinel, 0, coef)
+    assert bool((coef == 7.0).all())
+    codes = torch.zeros((wl.nt, 4, wl.nv), dtype=torch.uint8, device="cuda")
+    L.laph_make_sources(context(), lat, evecs, wl.nv, 0, 1, L.dilution(*tiny.dil), [], sentinel, codes)
+    assert bool((sentinel == 7.0 + 7.0j).all())
+    vh = wl.ns ** 3 * wl.nt // 2
+    x = torch.zeros((vh, 12, 1), dtype=torch.complex128, device="cuda")
+    with pytest.raises(L.LaphError) as e:
+        L.laph_dslash_eo(context(), lat, u, wl.m0, wl.csw, 0, L.HOP_CLOVINV, L.PREC_FP64, x, None, x, 0)
+    assert e.value.code == L.LAPH_ERR_ARG

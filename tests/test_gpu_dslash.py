@@ -5,8 +5,10 @@ The reference for output parity p, with q = 1 - p, is built from full-lattice fi
   apply     (K x)_p with x_p = z, x_q = in
   clovinv   A_pp^{-1} (D x)_p with x_p = 0, x_q = in   (A_pp inverted site by site)
   xpay      z - clovinv
-Right-hand-side counts cover the register-fed kernel (1, 5) and the copy-engine-fed
-kernel (multiples of 32), on a lattice whose sites do not fill the persistent grid evenly.
+Right-hand-side counts cover the register-fed kernel (1, 5, and 96, which is not a power
+of two) and the copy-engine-fed kernel (32: one RHS per lane; 64: two per lane; 128: two
+per lane with two warps per site), on lattices whose sites do not fill the persistent grid
+evenly.
 
 Tolerances: FP64 rel <= 1e-12 (same arithmetic, another summation order).  FP32: the
 inputs are rounded to FP32 before the reference sees them, so the error is the kernel's
@@ -75,7 +77,7 @@ MODES = {"clovinv": 0, "xpay": 1, "apply": 2}
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("mode", list(MODES))
-@pytest.mark.parametrize("nr", [1, 5, 32, 64])
+@pytest.mark.parametrize("nr", [1, 5, 32, 64, 96, 128])
 def test_hop_parity(lattice, prec, mode, nr):
     import torch
     L = lib()
