@@ -248,9 +248,10 @@ int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const void *links,
 
 /* RHS block the mixed solver's autotuner chose for a lattice of vh = V/2 sites, where nmax is
  * the largest candidate block that fitted (16, 32, 64 or 128, at most nrhs); 0 if no mixed
- * solve with rhs_block <= 0 has needed it in this context yet.  The tuner times the FP32
- * Schur operator and one reduction at each candidate on scratch fields once and keeps the
- * block with the lowest time per right-hand side (ties within 3 % go to the larger block). */
+ * solve with rhs_block <= 0 has needed it in this context yet.  The tuner times t = M s with
+ * the inner products <t, s>, <t, t> (the solver's own kernels) at each candidate on scratch
+ * fields once and keeps the block with the lowest time per right-hand side (ties within 3 %
+ * go to the larger block). */
 int laph_tuned_block(laph_ctx *ctx, int vh, int nmax);
 
 /* ------------------------------------------------------------------------

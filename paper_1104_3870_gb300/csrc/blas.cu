@@ -13,7 +13,7 @@ RedPlan red_plan(laph_ctx *ctx, long nrows, int nr) {
     while (nr * p.rpb * 2 <= 256) p.rpb *= 2;
     p.block = nr * p.rpb;
     long want = (nrows + p.rpb - 1) / p.rpb;
-    long cap = 4L * (ctx->sm_count > 0 ? ctx->sm_count : 152);
+    long cap = 8L * (ctx->sm_count > 0 ? ctx->sm_count : 152);   // enough warps to keep the loads in flight
     p.grid = (unsigned)(want < cap ? (want < 1 ? 1 : want) : cap);
     return p;
 }

@@ -306,7 +306,7 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
 // RHS block of the mixed solver when the caller leaves the choice to the library: among the
 // block sizes 16, 32, 64 and 128 that do not exceed nrhs and whose solver vectors fit in 60 % of
 // the free device memory, the one with the lowest time per right-hand side of one inner
-// iteration's operator work (the Schur operator, then one two-product reduction), measured
+// iteration's operator work (t = M s with <t, s> and <t, t>, fused where the shape allows), measured
 // with CUDA events on scratch fields once per lattice size and candidate set and cached in
 // the context.
 static int autotune_block(laph_ctx *ctx, const DiracOp &op, int nrhs, cudaStream_t s) {
@@ -335,10 +335,7 @@ static int autotune_block(laph_ctx *ctx, const DiracOp &op, int nrhs, cudaStream
     double best_t = 1e300;
     for (int nr : cand) {
         RedPlan pl = red_plan(ctx, nrows, nr);
-        auto once = [&]() {
-            schur_apply<float>(op, nr, a, b, t, s);
-            mrhs_dots<float>(ctx, pl, nrows, 2, b, a, b, b, nullptr, nullptr, red, s);
-        };
+        auto once = [&]() { schur_apply_tdots<float>(ctx, pl, nrows, op, nr, a, b, t, red, s); };
         once();
         LAPH_CUDA(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 3; ++rep) once();
