@@ -31,8 +31,11 @@ __global__ void red_kernel(long nrows, int nr, int rpb, Body body, c64 *partial)
     Acc acc[NRED];
 #pragma unroll
     for (int k = 0; k < NRED; ++k) acc[k] = {0, 0};
-    for (long row = (long)blockIdx.x * rpb + row0; row < nrows; row += (long)gridDim.x * rpb)
-        body(row * nr + r, r, acc);
+    // two rows per step (Body::two issues both rows' loads before either row's stores)
+    const long step = (long)gridDim.x * rpb;
+    long row = (long)blockIdx.x * rpb + row0;
+    for (; row + step < nrows; row += 2 * step) body.two(row * nr + r, (row + step) * nr + r, r, acc);
+    if (row < nrows) body(row * nr + r, r, acc);
 #pragma unroll
     for (int k = 0; k < NRED; ++k) sm[k * bd + tid] = cvt<double>(acc[k]);
     __syncthreads();
@@ -86,6 +89,10 @@ struct Dots1 {
     using Acc = cpx<T>;
     const cpx<T> *a0, *b0;
     __device__ void operator()(long i, int, Acc *acc) const { acc[0] += cmul_conj(a0[i], b0[i]); }
+    __device__ void two(long i, long j, int k, Acc *acc) const {
+        (*this)(i, k, acc);
+        (*this)(j, k, acc);
+    }
 };
 template <typename T>
 struct Dots2 {
@@ -94,6 +101,10 @@ struct Dots2 {
     __device__ void operator()(long i, int, Acc *acc) const {
         acc[0] += cmul_conj(a0[i], b0[i]);
         acc[1] += cmul_conj(a1[i], b1[i]);
+    }
+    __device__ void two(long i, long j, int k, Acc *acc) const {
+        (*this)(i, k, acc);
+        (*this)(j, k, acc);
     }
 };
 template <typename T>
@@ -104,6 +115,10 @@ struct Dots3 {
         acc[0] += cmul_conj(a0[i], b0[i]);
         acc[1] += cmul_conj(a1[i], b1[i]);
         acc[2] += cmul_conj(a2[i], b2[i]);
+    }
+    __device__ void two(long i, long j, int k, Acc *acc) const {
+        (*this)(i, k, acc);
+        (*this)(j, k, acc);
     }
 };
 
@@ -227,6 +242,20 @@ struct XRBody {
         r[i] = rn;
         acc[0] += cmul_conj(rhat[i], rn);
         acc[1] += cmul_conj(rn, rn);
+    }
+    __device__ void two(long i, long j, int k, Acc *acc) const {
+        const cpx<T> a = cvt<T>(sc.alpha[k]), w = cvt<T>(sc.omega[k]);
+        const cpx<T> xi = x[i], pi = p[i], si = sv[i], ti = t[i], hi = rhat[i];
+        const cpx<T> xj = x[j], pj = p[j], sj = sv[j], tj = t[j], hj = rhat[j];
+        const cpx<T> ri = si - w * ti, rj = sj - w * tj;
+        x[i] = xi + a * pi + w * si;
+        x[j] = xj + a * pj + w * sj;
+        r[i] = ri;
+        r[j] = rj;
+        acc[0] += cmul_conj(hi, ri);
+        acc[1] += cmul_conj(ri, ri);
+        acc[0] += cmul_conj(hj, rj);
+        acc[1] += cmul_conj(rj, rj);
     }
 };
 
