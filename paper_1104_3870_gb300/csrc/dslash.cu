@@ -161,9 +161,9 @@ __global__ void __launch_bounds__(256) hop_kernel(DiracOp op, int p, cpx<T> *__r
     long cb = tid / nr;
     int r = (int)(tid - cb * nr);
     if (cb >= g.Vh) return;
-    int c[4];
-    cb_coords(g, p, cb, c);
-    const int dims[4] = {g.ns, g.ns, g.ns, g.nt};
+    // neighbours from the table of prepare_f32_operands: forward mu then backward mu, ~j marks
+    // a hop across the time boundary (antiperiodic sign)
+    const int *nb8 = op.nbr + ((long)p * g.Vh + cb) * 8;
     cpx<T> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = {0, 0};
@@ -172,28 +172,24 @@ __global__ void __launch_bounds__(256) hop_kernel(DiracOp op, int p, cpx<T> *__r
         cpx<T> u[3][3], psi[12];
         // forward neighbour
         {
-            int cf[4] = {c[0], c[1], c[2], c[3]};
-            cf[mu] = (c[mu] + 1 == dims[mu]) ? 0 : c[mu] + 1;
-            long nb = site_of(g, cf) >> 1;
+            int j = __ldg(nb8 + mu);
+            T coef = j < 0 ? -(T)op.hw[mu] : (T)op.hw[mu];
+            long nb = j < 0 ? ~j : j;
             const cpx<T> *src = in + nb * 12 * nr + r;
 #pragma unroll
             for (int k = 0; k < 12; ++k) psi[k] = src[(long)k * nr];
             LinkLoad<T>::load(op, p, mu, cb, u);
-            T coef = (T)op.hw[mu];
-            if (mu == 3 && c[3] == g.nt - 1) coef = -coef;
             hop_dir<T>(mu, true, acc, psi, u, coef);
         }
         // backward neighbour
         {
-            int cbk[4] = {c[0], c[1], c[2], c[3]};
-            cbk[mu] = (c[mu] == 0) ? dims[mu] - 1 : c[mu] - 1;
-            long nb = site_of(g, cbk) >> 1;
+            int j = __ldg(nb8 + 4 + mu);
+            T coef = j < 0 ? -(T)op.hw[mu] : (T)op.hw[mu];
+            long nb = j < 0 ? ~j : j;
             const cpx<T> *src = in + nb * 12 * nr + r;
 #pragma unroll
             for (int k = 0; k < 12; ++k) psi[k] = src[(long)k * nr];
             LinkLoad<T>::load(op, 1 - p, mu, nb, u);
-            T coef = (T)op.hw[mu];
-            if (mu == 3 && c[3] == 0) coef = -coef;
             hop_dir<T>(mu, false, acc, psi, u, coef);
         }
     }
