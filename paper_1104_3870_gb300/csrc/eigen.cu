@@ -769,17 +769,22 @@ extern "C" int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *
             const long ts = (long)keep * n;
             dim3 gg((unsigned)((keep + 15) / 16), (unsigned)((keep + 15) / 16), nt);
             std::vector<double> one(nt, 1.0), zero(nt, 0.0);
-            for (int it = 0; it < 20 && !done; ++it, ++polish_iters) {
+            // passes continue while they gain: at most 100, and never after three passes in a row
+            // that each cut the worst residual by less than 10 %
+            double pol_prev = worst;
+            int pol_flat = 0;
+            for (int it = 0; it < 100 && !done && pol_flat < 3; ++it, ++polish_iters) {
                 // filter: T_k into F[(ncheb - k) % 3], T_0 = cur
-                auto fb = [&](int k) { return F[(ncheb - k) % 3]; };
+                const int npol = ncheb;
+                auto fb = [&](int k) { return F[(npol - k) % 3]; };
                 cheb_kernel<<<cg, 128, 0, s>>>(g, U, keep, cur, nullptr, fb(1), lz.ca, lz.cb, 1.0, 0, ts, ts);
                 LAPH_LAUNCH_CHECK();
-                for (int k = 2; k <= ncheb; ++k) {
+                for (int k = 2; k <= npol; ++k) {
                     const c64 *tm2 = (k == 2) ? cur : fb(k - 2);
                     cheb_kernel<<<cg, 128, 0, s>>>(g, U, keep, fb(k - 1), tm2, fb(k), lz.ca, lz.cb, 2.0, 1, ts, ts);
                     LAPH_LAUNCH_CHECK();
                 }
-                lz.matvecs += (long)ncheb * keep;
+                lz.matvecs += (long)npol * keep;
                 c64 *Yf = F[0];
                 // Loewdin: S = Yf^dag Yf = W diag(w) W^dag, Y = Yf W diag(w)^{-1/2}
                 gram_kernel<<<gg, 256, 0, s>>>(n, keep, Yf, Yf, Gk);
@@ -816,6 +821,8 @@ extern "C" int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *
                 worst = 0.0;
                 for (double r : h_res) worst = std::max(worst, std::isfinite(r) ? r : 1e300);
                 if (worst <= tol * 12.0) done = true;
+                pol_flat = (worst > 0.9 * pol_prev) ? pol_flat + 1 : 0;
+                pol_prev = std::min(pol_prev, worst);
             }
         }
         // outputs: ascending mu with the phase convention
