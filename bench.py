@@ -5,7 +5,10 @@ One step = one pass of the whole hot path over one batch of synthetic input:
 Laplacian eigenvectors of every slice (a1), Z4 diluted sources for two noises
 (a2), the batched solves of all diluted sources to FP64 true residual 1e-10
 (a3), sink coefficients (a4) and the pion / scalar / rho correlators (a5).
-Gauge preparation (stout smearing, a0) is setup and not timed.
+Gauge preparation (stout smearing, a0) is setup and not timed.  Steps are
+pipelined: a second library context computes the next batch's eigenvectors on
+its own stream while this batch's sources, solves, sinks and correlators run
+(--no-overlap runs the stages of each step one after another).
 
 Default workload: 16^3 x 32, xi = 3.5, N_v = 32, (TF, SF, LI8) at four source
 times (0, 8, 16, 24), two noises -> 256 diluted sources per step (seeded synthetic
@@ -49,7 +52,10 @@ def parse_args(argv=None):
     p.add_argument("--mode", choices=["mixed", "plain"], default="mixed")
     p.add_argument("--plain-sample", type=int, default=2, help="sources solved by the plain FP64 comparison")
     p.add_argument("--e2e-steps", type=int, default=2)
-    p.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per solver launch (0: all)")
+    p.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per solver launch (0: autotuned)")
+    p.add_argument("--no-overlap", action="store_true",
+                   help="run each step's stages one after another (default: the next batch's eigenvectors "
+                        "overlap this batch's solves)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--learned-sample", type=int, default=64, help="sources solved with the learned preconditioner")
     p.add_argument("--learned-pairs", type=int, default=64, help="(rho, phi) training pairs")
@@ -293,11 +299,57 @@ class PathStep:
         o = (ti * self.nnoise + k) * self.nb
         return slice(o, o + self.nb)
 
-    def run(self, u_in, ut_in, read_back=False, events=None):
+    def enable_overlap(self, eig_path):
+        """Pipelined steps: the eigenvectors of the next batch are computed by a second library
+        context on its own stream (FP64-bound kernels) while this batch's sources, solves (FP32
+        and memory bound), sinks and correlators run on the main stream.  Each step still does
+        the whole path's work: over K steps, K eigensolves and K solve stages."""
+        torch = self.torch
+        self.eig_path = eig_path
+        self.main_stream = torch.cuda.Stream()
+        self.eig_stream = torch.cuda.Stream()
+        self.evecs_next = torch.empty_like(self.evecs)
+        self.evals_next = torch.empty_like(self.evals)
+        self.primed = False
+
+    def run_overlapped(self, u_in, ut_in, read_back=False):
+        import threading
+        torch = self.torch
+        if not self.primed:   # the first batch's eigenvectors (outside any timed region)
+            with torch.cuda.stream(self.eig_stream):
+                self.eig_path.eigvecs(ut_in, self.evals_next, self.evecs_next)
+            self.eig_stream.synchronize()
+            self.primed = True
+        # this batch uses the vectors computed during the previous step
+        self.evecs, self.evecs_next = self.evecs_next, self.evecs
+        self.evals, self.evals_next = self.evals_next, self.evals
+        box = {}
+
+        def eig_lane():
+            try:
+                with torch.cuda.stream(self.eig_stream):
+                    box["rep"] = self.eig_path.eigvecs(ut_in, self.evals_next, self.evecs_next)[2]
+            except Exception as e:   # surfaced on the main thread below
+                box["err"] = e
+
+        th = threading.Thread(target=eig_lane)
+        th.start()
+        with torch.cuda.stream(self.main_stream):
+            self.run(u_in, ut_in, read_back=read_back, skip_eig=True)
+        th.join()
+        if "err" in box:
+            raise box["err"]
+        self.main_stream.wait_stream(self.eig_stream)
+        rep = box["rep"]
+        self.stats["eig"] = (rep.restarts, rep.matvecs, rep.max_resid)
+
+    def run(self, u_in, ut_in, read_back=False, events=None, skip_eig=False):
         p = self.path
         mark = (lambda i: events[i].record(self.torch.cuda.current_stream())) if events else (lambda i: None)
         mark(0)
-        _, _, rep = p.eigvecs(ut_in, self.evals, self.evecs)
+        if not skip_eig:
+            _, _, rep = p.eigvecs(ut_in, self.evals, self.evecs)
+            self.stats["eig"] = (rep.restarts, rep.matvecs, rep.max_resid)
         mark(1)
         for ti, bs in enumerate(self.bss):
             for k in range(self.nnoise):
@@ -317,7 +369,6 @@ class PathStep:
             self.corr_host.copy_(self.corr, non_blocking=True)
         self.stats["iters"] = [r.iters for r in reps]
         self.stats["resid"] = max(r.true_resid for r in reps)
-        self.stats["eig"] = (rep.restarts, rep.matvecs, rep.max_resid)
 
 
 def profiled_step(L, torch, st, u, ut):
@@ -363,8 +414,17 @@ def run_ours(args):
     nsrc, nb, nnoise = st.nsrc, st.nb, st.nnoise
     rhs, sol, corr_host, stats = st.rhs, st.sol, st.corr_host, st.stats
 
+    overlap = not args.no_overlap
+    eig_path = None
+    if overlap:
+        eig_path = LapHPath(spec, local)
+        st.enable_overlap(eig_path)
+
     def step(u_in, ut_in, read_back=False):
-        st.run(u_in, ut_in, read_back=read_back)
+        if overlap:
+            st.run_overlapped(u_in, ut_in, read_back=read_back)
+        else:
+            st.run(u_in, ut_in, read_back=read_back)
 
     for _ in range(args.warmup):
         step(u, ut)
@@ -374,7 +434,7 @@ def run_ours(args):
     L.laph_profile_reset()
     L.laph_profile_enable(1)
     launches0 = L.laph_launch_count()
-    stream = torch.cuda.current_stream()
+    stream = st.main_stream if overlap else torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -465,6 +525,7 @@ def run_ours(args):
                                    f"{(wl.dil_time, wl.dil_spin, wl.dil_laph)} at source times {list(wl.source_times)}, "
                                    f"{nnoise} noises x {nb} projectors each per replica",
                        "sources_per_step": nsrc, "solver": args.mode, "tol": 1e-10,
+                       "overlap": "next batch's eigenvectors beside this batch's solves" if overlap else "none",
                        "l2": "inputs larger than L2 (solver working set > 1 GB)", "parallelism": f"replicas{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "breakdown": breakdown,
             "variants": variants,
@@ -475,6 +536,8 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     path.close()
+    if eig_path is not None:
+        eig_path.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -60,7 +60,7 @@ void hop(const DiracOp &op, int p, HopMode mode, cpx<T> *out, const cpx<T> *in, 
 
 // FP32 hop with the packed operands of prepare_f32_operands (modes HOP_CLOVINV and HOP_CLOVINV_XPAY).
 // Throws LAPH_ERR_TIMEOUT (and clears the flag) when a TMA-fed stencil launch gave up waiting for a copy.
-void hop_timeout_check();
+void hop_timeout_check(cudaStream_t s);
 void hop_f32(const DiracOp &op, int p, HopMode mode, cpx<float> *out, const cpx<float> *in, const cpx<float> *z,
              int nr, cudaStream_t s);
 // The xpay hop out = z - A_pp^{-1} D in with the inner products <out, z> and <out, out> of every

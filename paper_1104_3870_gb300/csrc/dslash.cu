@@ -404,6 +404,6 @@ extern "C" int laph_dslash_eo(laph_ctx *ctx, const laph_lattice *lat, const void
         }
         o.commit(s);
         LAPH_CUDA(cudaStreamSynchronize(s));
-        hop_timeout_check();
+        hop_timeout_check(s);
     });
 }

@@ -504,12 +504,14 @@ static void hop3_modes(const DiracOp &op, int p, HopMode mode, float hws, float 
         launch_hop3<HOP_CLOVINV_XPAY, NS, RPT>(op, p, hws, hwt, out, in, z, nr, s);
 }
 
-void hop_timeout_check() {
-    int v = 0;
-    LAPH_CUDA(cudaMemcpyFromSymbol(&v, g_hop3_timeout, sizeof(int)));
+void hop_timeout_check(cudaStream_t s) {
+    int v = 0;   // read on the caller's stream, so that other streams are not serialised with it
+    LAPH_CUDA(cudaMemcpyFromSymbolAsync(&v, g_hop3_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    LAPH_CUDA(cudaStreamSynchronize(s));
     if (v) {   // 1: a copy wait gave up; 2: the shared-memory ring was misaligned (no copy issued)
         const int zero = 0;
-        LAPH_CUDA(cudaMemcpyToSymbol(g_hop3_timeout, &zero, sizeof(int)));
+        LAPH_CUDA(cudaMemcpyToSymbolAsync(g_hop3_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+        LAPH_CUDA(cudaStreamSynchronize(s));
         throw Error(LAPH_ERR_TIMEOUT, "a stencil copy wait gave up (device wait cap)");
     }
 }

@@ -94,7 +94,7 @@ static InnerStats bicgstab_schur(laph_ctx *ctx, const DiracOp &op, int nr, const
         if ((it + 1) % check_every == 0 || it + 1 == maxiter) {
             LAPH_CUDA(cudaMemcpyAsync(h_flags, sc.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, s));
             LAPH_CUDA(cudaStreamSynchronize(s));
-            hop_timeout_check();
+            hop_timeout_check(s);
             bool any = false;
             for (int k = 0; k < nr; ++k) any |= h_flags[k] != 0;
             if (!any) break;
@@ -411,7 +411,7 @@ extern "C" int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const v
         }
         o.commit(s);
         LAPH_CUDA(cudaStreamSynchronize(s));
-        hop_timeout_check();
+        hop_timeout_check(s);
         bool ok = true;
         for (int k = 0; k < nrhs; ++k) ok &= rep[k].status == LAPH_OK;
         if (report) std::copy(rep.begin(), rep.end(), report);
