@@ -37,6 +37,7 @@ typedef struct {
     const cplx *A;
     int ns, nt;
     double w[4];
+    int nthreads; /* threads splitting the site loop of one application (0 or 1: none) */
 } op_t;
 
 static void neighbours(const op_t *op, long s, int mu, long *fw, long *bw, double *sf, double *sb) {
@@ -56,9 +57,9 @@ static void neighbours(const op_t *op, long s, int mu, long *fw, long *bw, doubl
     *sb = (mu == 3 && t == 0) ? -1.0 : 1.0;
 }
 
-static void apply_K(const op_t *op, const cplx *in, cplx *out) {
-    long V = (long)op->ns * op->ns * op->ns * op->nt;
-    for (long s = 0; s < V; ++s) {
+/* out = K in on the sites [s0, s1). */
+static void apply_K_range(const op_t *op, const cplx *in, cplx *out, long s0, long s1) {
+    for (long s = s0; s < s1; ++s) {
         cplx acc[12];
         const cplx *a = op->A + s * 144;
         for (int i = 0; i < 12; ++i) {
@@ -94,6 +95,42 @@ static void apply_K(const op_t *op, const cplx *in, cplx *out) {
         }
         for (int i = 0; i < 12; ++i) out[s * 12 + i] = acc[i];
     }
+}
+
+typedef struct {
+    const op_t *op;
+    const cplx *in;
+    cplx *out;
+    long s0, s1;
+} range_t;
+
+static void *range_worker(void *arg) {
+    const range_t *r = (const range_t *)arg;
+    apply_K_range(r->op, r->in, r->out, r->s0, r->s1);
+    return NULL;
+}
+
+/* out = K in; the sites are split over op->nthreads threads when asked (every site's
+   arithmetic is the same either way). */
+static void apply_K(const op_t *op, const cplx *in, cplx *out) {
+    long V = (long)op->ns * op->ns * op->ns * op->nt;
+    int nth = op->nthreads;
+    if (nth <= 1) {
+        apply_K_range(op, in, out, 0, V);
+        return;
+    }
+    if (nth > 64) nth = 64;
+    pthread_t th[64];
+    range_t rg[64];
+    for (int i = 0; i < nth; ++i) {
+        rg[i].op = op;
+        rg[i].in = in;
+        rg[i].out = out;
+        rg[i].s0 = V * i / nth;
+        rg[i].s1 = V * (i + 1) / nth;
+        pthread_create(&th[i], NULL, range_worker, &rg[i]);
+    }
+    for (int i = 0; i < nth; ++i) pthread_join(th[i], NULL);
 }
 
 static cplx dotc(const cplx *a, const cplx *b, long n) {
@@ -145,7 +182,7 @@ static int bicgstab(const op_t *op, const cplx *b, cplx *x, double tol, int maxi
 
 void oracle_K_apply(const double *U, const double *A, int ns, int nt, double xi,
                     const double *in, double *out) {
-    op_t op = {(const cplx *)U, (const cplx *)A, ns, nt, {1.0 / xi, 1.0 / xi, 1.0 / xi, 1.0}};
+    op_t op = {(const cplx *)U, (const cplx *)A, ns, nt, {1.0 / xi, 1.0 / xi, 1.0 / xi, 1.0}, 1};
     apply_K(&op, (const cplx *)in, (cplx *)out);
 }
 
@@ -172,7 +209,7 @@ static void *worker(void *arg) {
 void oracle_bicgstab_batch(const double *U, const double *A, int ns, int nt, double xi,
                            const double *b, double *x, int nrhs, double tol, int maxiter,
                            int nthreads, int *iters, double *relres) {
-    op_t op = {(const cplx *)U, (const cplx *)A, ns, nt, {1.0 / xi, 1.0 / xi, 1.0 / xi, 1.0}};
+    op_t op = {(const cplx *)U, (const cplx *)A, ns, nt, {1.0 / xi, 1.0 / xi, 1.0 / xi, 1.0}, 1};
     if (nthreads < 1) nthreads = 1;
     if (nthreads > nrhs) nthreads = nrhs;
     pthread_t th[256];
@@ -183,4 +220,12 @@ void oracle_bicgstab_batch(const double *U, const double *A, int ns, int nt, dou
         pthread_create(&th[i], NULL, worker, &jobs[i]);
     }
     for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+}
+
+/* One BiCGStab solve of K x = b with the site loop of each application of K split over
+   nthreads threads; returns the iteration count. */
+int oracle_bicgstab_threaded(const double *U, const double *A, int ns, int nt, double xi, const double *b,
+                             double *x, double tol, int maxiter, int nthreads, double *relres) {
+    op_t op = {(const cplx *)U, (const cplx *)A, ns, nt, {1.0 / xi, 1.0 / xi, 1.0 / xi, 1.0}, nthreads};
+    return bicgstab(&op, (const cplx *)b, (cplx *)x, tol, maxiter, relres);
 }
