@@ -299,3 +299,19 @@ def test_bicgstab_vs_lu(tiny_dirac):
     kd = tiny_dirac.sparse().toarray()
     xl = scipy.linalg.lu_solve(scipy.linalg.lu_factor(kd), b.ravel())
     assert np.linalg.norm(x.ravel() - xl) / np.linalg.norm(xl) < 1e-10
+
+
+def test_threaded_oracle_solve_is_bit_identical():
+    """The opt-in site-split threads of the plain-C operator change no arithmetic: one
+    BiCGStab solve gives the same iterate bit for bit on 1 and 4 threads, and the same as
+    the per-right-hand-side batch solver."""
+    from oracle.fast import FastK
+    from oracle.pipeline import OraclePath
+    wl = synth.WORKLOADS["tiny_4x8"]
+    fk = FastK(OraclePath(wl).K)
+    b = synth.random_spinor(wl.ns, wl.nt, seed=99)
+    x1, i1, r1 = fk.solve_split(b, tol=1e-10, maxiter=1000, nthreads=1)
+    x4, i4, r4 = fk.solve_split(b, tol=1e-10, maxiter=1000, nthreads=4)
+    xb, ib, rb = fk.solve(b, tol=1e-10, maxiter=1000, nthreads=1)
+    assert i1 == i4 == ib and r1 == r4 == rb
+    assert np.array_equal(x1, x4) and np.array_equal(x1, xb)
