@@ -252,7 +252,7 @@ def learned_leg(L, torch, path, wl, u, rhs, args):
     sub = rhs[:n].clone()
     xs = torch.empty_like(sub)
     out = {"sample": n, "train_pairs": npairs, "train_epochs": args.learned_epochs, "train_batch": args.learned_batch,
-           "pairs_solve_s": pairs_s, "train_s": train_s, "loss_start": loss0, "loss_trained": loss1}
+           "pairs_solve_s": pairs_s, "train_s": train_s, "loss_start": loss0, "loss_trained": loss1, "_weights": w}
     stream = torch.cuda.current_stream()
     for name, ww in (("trained", w), ("start", w0)):
         wdev = torch.from_numpy(ww).cuda()
@@ -499,7 +499,9 @@ def run_ours(args):
            "h2d_bytes_per_step": int(u_h.numel() * u_h.element_size() * 2),
            "d2h_bytes_per_step": int(corr_host.numel() * corr_host.element_size())}
 
-    # plain FP64 comparison on a sample of the same sources: one right-hand side per launch
+    # plain FP64 comparison on a sample of the same sources: one right-hand side per launch.
+    # The variants run on this thread's current stream and are timed there.
+    stream = torch.cuda.current_stream()
     variants = {}
     if args.plain_sample > 0 and mode == L.MIXED_FP32:
         sub = rhs[:args.plain_sample].clone()
@@ -531,6 +533,33 @@ def run_ours(args):
 
     if args.learned_sample > 0 and mode == L.MIXED_FP32:
         variants["learned_fgcr"] = learned_leg(L, torch, path, wl, u, rhs, args)
+        w_trained = variants["learned_fgcr"].pop("_weights")
+    else:
+        w_trained = None
+
+    # single-change ablations on small samples of the same sources: each turns on one of
+    # precision (FP32 inner), batching (many RHS per launch) or the learned preconditioner
+    if args.plain_sample > 0 and mode == L.MIXED_FP32:
+        def timed_solve(n, prm):
+            sub = rhs[:n].clone()
+            xs = torch.empty_like(sub)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            reps = L.dirac_solve_batch(path.ctx, path.lat, u, wl.m0, wl.csw, sub, xs, n, prm)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            return {"sources_per_s": n / (a0.elapsed_time(a1) / 1000.0), "sample": n,
+                    "iters_mean": float(np.mean([r.iters for r in reps])),
+                    "true_resid_max": max(r.true_resid for r in reps)}
+        abl = {"precision_only: mixed FP32/FP64, one RHS per launch":
+               timed_solve(2, L.solver_params(mode=L.MIXED_FP32, rhs_block=1)),
+               "batching_only: plain FP64, 8 RHS per launch":
+               timed_solve(8, L.solver_params(mode=L.PLAIN_FP64, rhs_block=8))}
+        if w_trained is not None:
+            abl["learned_only: learned FGCR, one RHS per launch"] = timed_solve(
+                2, L.solver_params(mode=L.LEARNED, weights=torch.from_numpy(w_trained).cuda(), rhs_block=1))
+        variants["ablations"] = abl
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
