@@ -37,7 +37,12 @@
  *  * ns and nt must be even (even-odd ordering); ns >= 2, nt >= 2.
  *  * Calls are issued on `stream` (a cudaStream_t; NULL is the legacy default
  *    stream).  A call returns after its work is queued unless it writes host
- *    memory or a report, in which case it synchronises `stream` first.
+ *    memory or a report, in which case it synchronises `stream` first; the
+ *    eigensolver and the solvers also synchronise `stream` for their
+ *    host-side convergence checks.  Nothing is issued on any other stream.
+ *  * A context (its workspace and autotune cache) serves one host thread at a
+ *    time; separate contexts may run concurrently on separate streams of the
+ *    same GPU (the measurement helpers below are shared and thread-safe).
  *  * Return value: LAPH_OK or an error code; laph_last_error() then gives a
  *    message (thread-local).  No C++ exception crosses the ABI.
  */
