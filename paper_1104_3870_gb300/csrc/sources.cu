@@ -122,9 +122,10 @@ extern "C" int laph_make_sources(laph_ctx *ctx, const laph_lattice *lat, const v
         std::vector<int> hb(nb);
         if (nb) {
             LAPH_REQUIRE(b_list != nullptr, "b_list is null");
-            if (is_device_ptr(b_list))
-                LAPH_CUDA(cudaMemcpy(hb.data(), b_list, sizeof(int) * nb, cudaMemcpyDeviceToHost));
-            else
+            if (is_device_ptr(b_list)) {   // ordered on the caller's stream, then read on the host
+                LAPH_CUDA(cudaMemcpyAsync(hb.data(), b_list, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
+                LAPH_CUDA(cudaStreamSynchronize(s));
+            } else
                 std::copy(b_list, b_list + nb, hb.begin());
         }
         std::vector<uint8_t> m = dilution_masks(*dil, g.nt, nv, hb.data(), nb);
