@@ -229,10 +229,15 @@ def laph_eigvecs(ctx, lat, links3d, nv, evals, evecs, params=None, stream=None, 
 
 
 def laph_make_sources(ctx, lat, evecs, nv, noise_id, config_id, dil, b_list, rhs, noise=None, stream=None):
-    b = np.ascontiguousarray(np.asarray(b_list, dtype=np.int32))
+    if hasattr(b_list, "data_ptr"):   # an int32 tensor, host or device, passed as it is
+        if str(b_list.dtype) != "torch.int32":
+            raise ValueError("b_list tensors must be int32")
+        bptr, nb = _ptr(b_list), int(b_list.numel())
+    else:
+        b = np.ascontiguousarray(np.asarray(b_list, dtype=np.int32))
+        bptr, nb = b.ctypes.data, len(b)
     _check(_lib.laph_make_sources(ctx.ptr, ctypes.byref(lat), _ptr(evecs), int(nv), int(noise_id), int(config_id),
-                                  ctypes.byref(dil), b.ctypes.data, len(b), _ptr(rhs), _ptr(noise),
-                                  _stream(stream)))
+                                  ctypes.byref(dil), bptr, nb, _ptr(rhs), _ptr(noise), _stream(stream)))
 
 
 def solver_params(tol=1e-10, maxiter=100000, mode=MIXED_FP32, rhs_block=0, inner_tol=0.0, fallback=1,

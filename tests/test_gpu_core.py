@@ -142,6 +142,11 @@ def test_sources_and_noise(tiny, dil):
     rho = onoise.z4_values(onoise.z4_codes(nt, nv, 3, wl.config_id))
     ref = np.stack([olaph.dirac_rhs(tiny.evecs, rho, dil, b) for b in bs])
     assert np.abs(host(rhs) - ref).max() < 1e-13
+    # the projector list may also live in device memory
+    rhs2 = torch.empty_like(rhs)
+    L.laph_make_sources(context(), L.lattice(wl.ns, wl.nt, wl.xi), dev(tiny.evecs), nv, 3, wl.config_id,
+                        L.dilution(*dil), torch.tensor(bs, dtype=torch.int32, device="cuda"), rhs2, codes)
+    assert torch.equal(rhs2, rhs)
 
 
 def test_sinks_parity(tiny):
