@@ -534,8 +534,10 @@ void solve_block_learned(laph_ctx *ctx, const DiracOp &op, const float *weights,
         bool all = true;
         for (int k = 0; k < nr; ++k) {
             double rn = std::sqrt(h[k].re + h[nr + k].re);
-            rel[k] = bn[k] > 0 ? rn / bn[k] : 0.0;
-            if (!(rel[k] <= prm.tol)) {
+            // a right-hand side that is not finite is reported as not converged and left alone
+            const bool bad = !std::isfinite(bn[k]);
+            rel[k] = bad ? std::nan("") : (bn[k] > 0 ? rn / bn[k] : 0.0);
+            if (!(rel[k] <= prm.tol) && !bad) {
                 all = false;
                 worst = std::max(worst, std::isfinite(rel[k]) ? rel[k] : 1e300);
             }

@@ -146,6 +146,13 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
     LAPH_CUDA(cudaStreamSynchronize(s));
     std::vector<double> bnorm(nr);
     for (int k = 0; k < nr; ++k) bnorm[k] = std::sqrt(h_red[k].re + h_red[nr + k].re);
+    // a right-hand side that is not finite cannot be solved: it is reported as not converged
+    // (true residual NaN) and takes no further part in the cycles
+    std::vector<int> bad(nr, 0);
+    for (int k = 0; k < nr; ++k) bad[k] = !std::isfinite(bnorm[k]);
+    auto rel_of = [&](int k, double rn) {
+        return bad[k] ? std::nan("") : (bnorm[k] > 0 ? rn / bnorm[k] : 0.0);
+    };
 
     LAPH_CUDA(cudaMemsetAsync(xe, 0, hb, s));
     const double tol = prm.tol;
@@ -162,8 +169,8 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
             LAPH_CUDA(cudaMemcpyAsync(xo, to, hb, cudaMemcpyDeviceToDevice, s));
             LAPH_CUDA(cudaMemcpyAsync(re, bh, hb, cudaMemcpyDeviceToDevice, s));
             for (int k = 0; k < nr; ++k) {
-                rel[k] = bnorm[k] > 0 ? 1.0 : 0.0;
-                if (rel[k] > tol) {
+                rel[k] = rel_of(k, bnorm[k]);
+                if (!bad[k] && rel[k] > tol) {
                     all = false;
                     worst = 1.0;
                 }
@@ -189,8 +196,8 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
                     stop = true;
                     for (int k = 0; k < nr; ++k) {
                         const double rn = std::sqrt(h_red[k].re);
-                        const double re_rel = bnorm[k] > 0 ? rn / bnorm[k] : 0.0;
-                        if (!(re_rel <= tol) && !handed[k]) stop = false;
+                        const double re_rel = rel_of(k, rn);
+                        if (!(re_rel <= tol) && !handed[k] && !bad[k]) stop = false;
                     }
                 }
                 if (!stop) {
@@ -202,8 +209,8 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
             }
             for (int k = 0; k < nr; ++k) {
                 double rn = std::sqrt(h_red[k].re + h_red[nr + k].re);
-                rel[k] = bnorm[k] > 0 ? rn / bnorm[k] : 0.0;
-                if (!(rel[k] <= tol)) {
+                rel[k] = rel_of(k, rn);
+                if (!(rel[k] <= tol) && !bad[k]) {
                     stall[k] = (cyc > 1 && !(rel[k] <= 0.5 * prev[k])) ? stall[k] + 1 : 0;
                     if (prm.fallback && stall[k] >= 3) handed[k] = 1;
                     if (!handed[k]) {
@@ -223,7 +230,7 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
         LAPH_CUDA(cudaStreamSynchronize(s));
         for (int k = 0; k < nr; ++k) {
             double rn = std::sqrt(h_red[k].re);
-            bool done = rel[k] <= tol || handed[k] || !(rn > 0.0) || !std::isfinite(rn);
+            bool done = rel[k] <= tol || handed[k] || bad[k] || !(rn > 0.0) || !std::isfinite(rn);
             h_scale[k] = done ? 0.0 : 1.0 / rn;   // into the inner precision
             h_scale[nr + k] = done ? 0.0 : rn;    // back into x_e
             if (!done) outer[k] += 1;
@@ -286,7 +293,7 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
         LAPH_CUDA(cudaStreamSynchronize(s));
         for (int k = 0; k < nr; ++k) {
             if (!fell[k]) continue;
-            rel[k] = bnorm[k] > 0 ? std::sqrt(h_red[k].re + h_red[nr + k].re) / bnorm[k] : 0.0;
+            rel[k] = rel_of(k, std::sqrt(h_red[k].re + h_red[nr + k].re));
             iters[k] += cg_it[k];
         }
     }

@@ -255,3 +255,24 @@ def test_empty_inputs(tiny):
     with pytest.raises(L.LaphError) as e:
         L.laph_dslash_eo(context(), lat, u, wl.m0, wl.csw, 0, L.HOP_CLOVINV, L.PREC_FP64, x, None, x, 0)
     assert e.value.code == L.LAPH_ERR_ARG
+
+
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_solve_nan_rhs_is_reported(tiny, mode):
+    """A right-hand side carrying a NaN (a host-side injected fault) is reported as not
+    converged with a NaN true residual; the other right-hand sides of its block still reach
+    the tolerance."""
+    L = lib()
+    wl = tiny.wl
+    b = synth.random_spinor(wl.ns, wl.nt, seed=58, nrhs=3)
+    b[1, 0, 0, 0, 0, 0, 0] = np.nan
+    sol = empty(b.shape, dev(b).dtype)
+    m = L.PLAIN_FP64 if mode == "plain" else L.MIXED_FP32
+    reps = L.dirac_solve_batch(context(), L.lattice(wl.ns, wl.nt, wl.xi), dev(tiny.u), wl.m0, wl.csw, dev(b), sol,
+                               3, L.solver_params(tol=1e-10, mode=m, rhs_block=3), allow_not_converged=True)
+    assert reps[1].status == L.LAPH_ERR_NOT_CONVERGED and np.isnan(reps[1].true_resid)
+    x = host(sol)
+    x_lu, _ = tiny.solve(b[[0, 2]], "lu")
+    for i, k in enumerate((0, 2)):
+        assert reps[k].status == 0 and reps[k].true_resid <= 1e-10
+        assert np.linalg.norm(x[k] - x_lu[i]) / np.linalg.norm(x_lu[i]) < 1e-8
