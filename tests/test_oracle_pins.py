@@ -315,3 +315,21 @@ def test_threaded_oracle_solve_is_bit_identical():
     xb, ib, rb = fk.solve(b, tol=1e-10, maxiter=1000, nthreads=1)
     assert i1 == i4 == ib and r1 == r4 == rb
     assert np.array_equal(x1, x4) and np.array_equal(x1, xb)
+
+
+def test_inversion_counts_match_the_paper():
+    """The oracle's projector counts reproduce the inversion counts the paper prints (Sec. II;
+    fixture tests/golden/inversion_counts.json): projectors solved per noise are the
+    time projectors containing a source time (or all of them) x spin x eigenvector ones."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    data = json.load(open(os.path.join(here, "golden", "inversion_counts.json")))
+    per = []
+    for c in data["cases"]:
+        if "total" in c:
+            assert 5 * per[0] + 2 * per[1] == c["total"]
+            continue
+        nT, nS, nL = dl.counts(tuple(tuple(d) for d in c["dil"]), c["nt"], c["nv"])
+        n_time = c["source_times"] if c["source_times"] else nT   # full time dilution at chosen t0 only
+        n = n_time * nS * nL
+        assert n == c["inversions"], c["what"]
+        per.append(n)
