@@ -113,11 +113,13 @@ _sig = {
     "laph_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
+_missing = [n for n in _sig if not hasattr(_lib, n)]
+if _missing:
+    raise ImportError(f"{LIB} lacks {', '.join(_missing)}: rebuild with paper_1104_3870_gb300.build")
 for _name, (_res, _args) in _sig.items():
-    if hasattr(_lib, _name):
-        f = getattr(_lib, _name)
-        f.restype = _res
-        f.argtypes = _args
+    f = getattr(_lib, _name)
+    f.restype = _res
+    f.argtypes = _args
 
 
 def exported_symbols():
