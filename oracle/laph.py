@@ -27,6 +27,15 @@ noises; lines 1 and 3 are the gamma_5-swapped lines):
     X = sum_{b1..b4} M^[b1 b4](phibar_1, phi_4; t_F) M^[b3 b2](phibar_3, phi_2; t_F)
                      M^[b1 b2](rhobar_1, rho_2; t_0)^* M^[b3 b4](rhobar_3, rho_4; t_0)^*.
 
+Momentum (Sec. III, the phase of Eq. (mesonfunc) without displacement): an operator
+destroying momentum p carries sum_x e^{-i p.x}, p = 2 pi (p_x, p_y, p_z) / N_s with
+integer components; the sink function M_l(tF) and the source function M_lbar(t0),
+conjugated in Eq. (mesoncorr), both take that phase for the same p (reading: lbar is
+the creation operator of the same momentum, so conj(M_lbar) carries e^{+i p.x}).
+In LapH coordinates the phase enters through the overlap matrices
+    Phi_p(t)[n, n'] = sum_{x,c} V(t,n,x,c)^* e^{-i p.x} V(t,n',x,c),
+which are the identity at p = 0.
+
 This module works with full site-space fields (it builds varrho and varphi on
 the lattice and sums over sites), an independent route from the coefficient-
 space contractions of the CUDA path.
@@ -94,14 +103,31 @@ def spin_mul(m: np.ndarray, f: np.ndarray) -> np.ndarray:
     return np.einsum("ab,...bc->...ac", m, f)
 
 
-def meson_functions(a_list, b_list, c: np.ndarray) -> np.ndarray:
-    """M[b1, b2, t] = sum_{x,colour} sum_{alpha beta} a^[b1]_alpha(x,t)^* c_{alpha beta} b^[b2]_beta(x,t).
+def mom_phase(ns: int, mom) -> np.ndarray:
+    """e^{-i p.x} on one time slice, p = 2 pi mom / N_s, indexed like the slice's sites
+    ((z N_s + y) N_s + x, x fastest)."""
+    z, y, x = np.meshgrid(np.arange(ns), np.arange(ns), np.arange(ns), indexing="ij")
+    px, py, pz = mom
+    return np.exp(-2j * np.pi * (px * x + py * y + pz * z) / ns).ravel()
 
-    a_list, b_list: arrays [nb, t, z, y, x, 4, 3]."""
+
+def mom_overlaps(evecs: np.ndarray, mom) -> np.ndarray:
+    """Phi_p(t)[n, n'] = sum_{x,c} V(t,n,x,c)^* e^{-i p.x} V(t,n',x,c), [nt][nv][nv]."""
+    nt, nv, v3, _ = evecs.shape
+    ph = mom_phase(round(v3 ** (1.0 / 3.0)), mom)
+    return np.einsum("tnxc,x,tmxc->tnm", np.conj(evecs), ph, evecs)
+
+
+def meson_functions(a_list, b_list, c: np.ndarray, mom=None) -> np.ndarray:
+    """M[b1, b2, t] = sum_{x,colour} e^{-i p.x} sum_{alpha beta} a^[b1]_alpha(x,t)^* c_{alpha beta} b^[b2]_beta(x,t).
+
+    a_list, b_list: arrays [nb, t, z, y, x, 4, 3]; mom: integer 3-vector (None: p = 0)."""
     nb1, nt = a_list.shape[0], a_list.shape[1]
     a = a_list.reshape(nb1, nt, -1, 4, 3)
     b = b_list.reshape(b_list.shape[0], nt, -1, 4, 3)
     cb = np.einsum("ab,ntxbc->ntxac", c, b)
+    if mom is not None:
+        cb = cb * mom_phase(a_list.shape[2], mom)[None, None, :, None, None]
     return np.einsum("ptxac,qtxac->pqt", np.conj(a), cb)
 
 
@@ -123,13 +149,14 @@ class Line:
         return spin_mul(G5G4, self.varphi)
 
 
-def meson_connected(line1: Line, line2: Line, t0: int, channel: str) -> np.ndarray:
-    """C(dt), dt = (t_F - t_0) mod N_t, of Eq. (mesoncorr) first term for one source time."""
+def meson_connected(line1: Line, line2: Line, t0: int, channel: str, mom=None) -> np.ndarray:
+    """C(dt), dt = (t_F - t_0) mod N_t, of Eq. (mesoncorr) first term for one source time,
+    at momentum mom (None: zero momentum)."""
     nt = line1.varrho.shape[1]
     out = np.zeros(nt, dtype=complex)
     for c in channel_c(channel):
-        msink = meson_functions(line1.varphi_bar, line2.varphi, c)       # [b1, b2, tF]
-        msrc = meson_functions(line1.varrho_bar, line2.varrho, c)[:, :, t0]
+        msink = meson_functions(line1.varphi_bar, line2.varphi, c, mom)       # [b1, b2, tF]
+        msrc = meson_functions(line1.varrho_bar, line2.varrho, c, mom)[:, :, t0]
         ct = -np.einsum("pqt,pq->t", msink, np.conj(msrc))
         out += np.roll(ct, -t0)
     return out / len(channel_c(channel))
@@ -168,15 +195,23 @@ def exact_G(evecs: np.ndarray, kinv: np.ndarray) -> np.ndarray:
     return (w.conj().T @ (kinv @ (g4 @ w))).reshape(nt, 4, nv, nt, 4, nv)
 
 
-def exact_meson_connected(G: np.ndarray, t0: int, channel: str) -> np.ndarray:
-    """C(t_F, t_0) = - sum c_{ab} c^*_{a'b'} G[t0 a' m; tF a n] G[tF b n; t0 b' m], dt-indexed."""
+def exact_meson_connected(G: np.ndarray, t0: int, channel: str, phi=None) -> np.ndarray:
+    """C(t_F, t_0) = - sum c_{ab} c^*_{a'b'} G[t0 a' m; tF a n] G[tF b n; t0 b' m], dt-indexed.
+
+    With momentum overlaps phi = Phi_p [nt][nv][nv] the LapH indices of the two lines meet
+    through them instead of directly:
+        - sum c_{ab} c^*_{a'b'} Phi_p(t0)[m, m']^* Phi_p(tF)[n, n'] G[t0 a' m; tF a n] G[tF b n'; t0 b' m']."""
     nt = G.shape[0]
     out = np.zeros(nt, dtype=complex)
     for c in channel_c(channel):
         for tf in range(nt):
             g_src_snk = G[t0, :, :, tf, :, :]     # [a', m, a, n]
             g_snk_src = G[tf, :, :, t0, :, :]     # [b, n, b', m]
-            out[(tf - t0) % nt] += -np.einsum("ab,pq,pman,bnqm->", c, np.conj(c), g_src_snk, g_snk_src)
+            if phi is None:
+                out[(tf - t0) % nt] += -np.einsum("ab,pq,pman,bnqm->", c, np.conj(c), g_src_snk, g_snk_src)
+            else:
+                out[(tf - t0) % nt] += -np.einsum("ab,pq,mM,nN,pman,bNqM->", c, np.conj(c), np.conj(phi[t0]),
+                                                  phi[tf], g_src_snk, g_snk_src)
     return out / len(channel_c(channel))
 
 
