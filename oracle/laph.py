@@ -36,6 +36,17 @@ In LapH coordinates the phase enters through the overlap matrices
     Phi_p(t)[n, n'] = sum_{x,c} V(t,n,x,c)^* e^{-i p.x} V(t,n',x,c),
 which are the identity at p = 0.
 
+Same-time lines (second term of Eq. (mesoncorr), isoscalar mesons): each line closes on
+one time slice, and the b sums of the two meson functions run separately:
+    D(t_F - t_0) = sum_{b1} M^[b1 b1](varrho_1, varphi_1; t_F) (sum_{b2} M^[b2 b2](varphi_2, varrho_2; t_0))^*.
+The paper names the two diagrams "fwd" (first term) and "smt" (second term) and, for its
+isoscalars made of the two light flavours, plots their sum.  Reading taken for the
+flavour weights: the operator (u-bar Gamma u + d-bar Gamma d)/sqrt(2) with degenerate u, d
+gives the delta factors of Eq. (mesoncorr) the sums 1 (first term) and 2 (second term),
+so C_isoscalar = fwd + 2 smt.  For the scalar the "smt" part has its vacuum expectation
+value removed: smt - <L_1> <L_2>^*, with <L> the loop averaged over configurations, time
+slices and noises.
+
 This module works with full site-space fields (it builds varrho and varphi on
 the lattice and sums over sites), an independent route from the coefficient-
 space contractions of the CUDA path.
@@ -162,6 +173,28 @@ def meson_connected(line1: Line, line2: Line, t0: int, channel: str, mom=None) -
     return out / len(channel_c(channel))
 
 
+def meson_loops(line: Line, channel: str, mom=None, reverse=False) -> np.ndarray:
+    """Same-time line closed on each slice: L_c(t) = sum_b M^[bb](varrho, varphi; t), or with
+    reverse M^[bb](varphi, varrho; t), one row per c of the channel, [nc][nt].  Every t must
+    be covered by the line's projectors (time interlacing with all of them solved)."""
+    a, b = (line.varphi, line.varrho) if reverse else (line.varrho, line.varphi)
+    return np.array([np.einsum("bbt->t", meson_functions(a, b, c, mom)) for c in channel_c(channel)])
+
+
+def meson_disconnected(line1: Line, line2: Line, t0: int, channel: str, mom=None) -> np.ndarray:
+    """Second term of Eq. (mesoncorr) for one source time, dt-indexed, averaged over the c of
+    the channel: L_1(t0 + dt) conj(L_2(t0)) with L_1 from (varrho_1, varphi_1) and L_2 from
+    (varphi_2, varrho_2)."""
+    l1 = meson_loops(line1, channel, mom)
+    l2 = meson_loops(line2, channel, mom, reverse=True)
+    return np.mean(np.roll(l1, -t0, axis=1) * np.conj(l2[:, t0])[:, None], axis=0)
+
+
+def isoscalar_meson(fwd: np.ndarray, smt: np.ndarray, vev=None) -> np.ndarray:
+    """fwd + 2 (smt - vev): two degenerate light flavours; vev = <L_1> <L_2>^* (scalar only)."""
+    return fwd + 2.0 * (smt - (0.0 if vev is None else vev))
+
+
 def pipi_i2(l1: Line, l2: Line, l3: Line, l4: Line, t0: int) -> np.ndarray:
     """I = 2 two-pion correlator D - X for one source time (see module docstring)."""
     nt = l1.varrho.shape[1]
@@ -213,6 +246,30 @@ def exact_meson_connected(G: np.ndarray, t0: int, channel: str, phi=None) -> np.
                 out[(tf - t0) % nt] += -np.einsum("ab,pq,mM,nN,pman,bNqM->", c, np.conj(c), np.conj(phi[t0]),
                                                   phi[tf], g_src_snk, g_snk_src)
     return out / len(channel_c(channel))
+
+
+def exact_loops(G: np.ndarray, channel: str, phi=None, reverse=False) -> np.ndarray:
+    """Full-dilution limit of meson_loops, [nc][nt]:
+        L_c(t) = sum c_{ab} Phi(t)[n, n'] G[t b n'; t a n]            (varrho, varphi)
+        L_c(t) = sum c_{ab} Phi(t)[n, n'] conj(G[t a n; t b n'])      (reverse: varphi, varrho)
+    with Phi = 1 at zero momentum."""
+    nt, nv = G.shape[0], G.shape[2]
+    out = np.zeros((len(channel_c(channel)), nt), dtype=complex)
+    for i, c in enumerate(channel_c(channel)):
+        for t in range(nt):
+            g = G[t, :, :, t, :, :]                         # [a, n, b, n']
+            ph = np.eye(nv) if phi is None else phi[t]
+            if reverse:
+                out[i, t] = np.einsum("ab,nN,anbN->", c, ph, np.conj(g))
+            else:
+                out[i, t] = np.einsum("ab,nN,bNan->", c, ph, g)
+    return out
+
+
+def exact_meson_disconnected(G: np.ndarray, t0: int, channel: str, phi=None) -> np.ndarray:
+    l1 = exact_loops(G, channel, phi)
+    l2 = exact_loops(G, channel, phi, reverse=True)
+    return np.mean(np.roll(l1, -t0, axis=1) * np.conj(l2[:, t0])[:, None], axis=0)
 
 
 def exact_pipi_i2(G: np.ndarray, t0: int) -> np.ndarray:
