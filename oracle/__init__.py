@@ -22,6 +22,7 @@ Modules:
   noise      Philox4x32-10 counter generator and Z4 LapH noise
   dilution   time/spin/LapH dilution projectors
   dirac      anisotropic Wilson-clover matrix K, BiCGStab, dense solves
-  laph       sources, sinks, meson functions and correlators
+  laph       sources, sinks, meson functions and correlators (momentum, same-time lines)
+  wick       Wick's theorem for products of LapH bilinears (brute-force correlators)
   precond    gauge-covariant learned preconditioner (forward/backward)
 """

@@ -1,0 +1,96 @@
+"""Wick's theorem written out for products of quark bilinears in LapH coordinates.
+
+Test infrastructure: the brute-force reference for the diagram bookkeeping of Sec. III
+(meson functions joined by quark lines, Eq. (mesoncorr) and the two-meson figures).
+
+A bilinear is B = sum_{i,j} M[i, j] qbar_f(i) q_g(j), with i, j compound (t, alpha, n)
+indices of the whole LapH space (index (t * 4 + alpha) * N_v + n) and f, g flavour
+labels.  With <q_g(j) qbar_f(i)> = delta_{fg} Q(j, i) and every bilinear Grassmann-even,
+Gaussian Grassmann integration gives
+    < B_1 ... B_m > = (-1)^m sum_{i, j} prod_k M_k[i_k, j_k] det[ Q(j_k, i_l) delta_{g_k f_l} ]_{k,l},
+the (-1)^m from writing qbar q = -q qbar.  Expanding the determinant over permutations
+sigma, each term factorises over the cycles of sigma:
+    (-1)^m sgn(sigma) prod_{cycles (k, sigma k, sigma^2 k, ...)} tr(M_k Q M_{sigma k} Q ...),
+and vanishes unless the flavour of q in B_k equals that of qbar in B_{sigma k} for every k.
+Q is the LapH propagator V_s^dag Omega^{-1} V_s (degenerate flavours share it).
+
+Operators follow the paper's conventions: the sink meson function of a bilinear
+c_{alpha beta} qbar^A_alpha q^B_beta at momentum p carries e^{-i p.x} (Sec. III), which in
+LapH coordinates is Phi_p(t) = V^dag e^{-i p.x} V between the colour-space indices; the
+matching source operator is c*_{alpha beta} qbar^B_beta q^A_alpha with e^{+i p.x}, that is
+Phi_{-p}.
+"""
+import itertools
+
+import numpy as np
+
+
+def lapH_index(nt, nv, t, alpha):
+    """Slice of the compound indices (t, alpha, 0..nv-1)."""
+    base = (t * 4 + alpha) * nv
+    return slice(base, base + nv)
+
+
+def sink_bilinear(nt, nv, t, c, phi_t, qbar_flavour, q_flavour):
+    """sum_{alpha beta} c_{alpha beta} sum_{n n'} phi_t[n, n'] qbar(t, alpha, n) q(t, beta, n')."""
+    m = np.zeros((nt * 4 * nv, nt * 4 * nv), dtype=complex)
+    for a in range(4):
+        for b in range(4):
+            m[lapH_index(nt, nv, t, a), lapH_index(nt, nv, t, b)] = c[a, b] * phi_t
+    return (m, qbar_flavour, q_flavour)
+
+
+def source_bilinear(nt, nv, t, c, phi_minus_t, qbar_flavour_of_sink, q_flavour_of_sink):
+    """Source partner of sink_bilinear(c, p, A, B): sum c*_{alpha beta} Phi_{-p}[n, n'] qbar^B(t, beta, n) q^A(t, alpha, n')."""
+    m = np.zeros((nt * 4 * nv, nt * 4 * nv), dtype=complex)
+    for a in range(4):
+        for b in range(4):
+            m[lapH_index(nt, nv, t, b), lapH_index(nt, nv, t, a)] = np.conj(c[a, b]) * phi_minus_t
+    return (m, q_flavour_of_sink, qbar_flavour_of_sink)
+
+
+def _cycles(perm):
+    seen, out = set(), []
+    for k in range(len(perm)):
+        if k in seen:
+            continue
+        cyc, j = [], k
+        while j not in seen:
+            seen.add(j)
+            cyc.append(j)
+            j = perm[j]
+        out.append(cyc)
+    return out
+
+
+def _sign(perm):
+    return (-1) ** sum(len(c) - 1 for c in _cycles(perm))
+
+
+def expect(bilinears, Q):
+    """< B_1 ... B_m > by the permutation expansion above; bilinears = [(M, qbar_flavour, q_flavour)]."""
+    m = len(bilinears)
+    mq = [b[0] @ Q for b in bilinears]
+    total = 0.0 + 0.0j
+    for perm in itertools.permutations(range(m)):
+        # q of B_k contracts with qbar of B_{perm[k]}
+        if any(bilinears[k][2] != bilinears[perm[k]][1] for k in range(m)):
+            continue
+        term = 1.0 + 0.0j
+        for cyc in _cycles(perm):
+            prod = mq[cyc[0]]
+            for k in cyc[1:]:
+                prod = prod @ mq[k]
+            term *= np.trace(prod)
+        total += _sign(perm) * term
+    return (-1) ** m * total
+
+
+def correlator(sink_terms, source_terms, Q):
+    """< O_sink O_source > for O = sum_r w_r prod(bilinears_r): sink_terms, source_terms are
+    lists of (weight, [bilinears])."""
+    out = 0.0 + 0.0j
+    for ws, bs in sink_terms:
+        for wr, br in source_terms:
+            out += ws * wr * expect(list(bs) + list(br), Q)
+    return out

@@ -1,0 +1,209 @@
+"""Pins of the brute-force Wick reference (oracle/wick.py) and, through it, of the signs
+and flavour weights of the oracle's correlator formulas.
+
+* the permutation formula for < B_1 ... B_m > equals a literal Gaussian Grassmann
+  integral, < X > = int X e^{-qbar A q} / int e^{-qbar A q}, computed in the exterior
+  algebra of 2 N generators on a tiny two-flavour space (m = 1..4, mixed flavours);
+  the two-point function of that integral is <q_j qbar_i> = (A^{-1})_{ji};
+* on a 4^3 x 4 lattice with Q = G = V_s^dag Omega^{-1} V_s:
+  - the connected meson correlator (first term of Eq. (mesoncorr), sign included) of a
+    flavour non-singlet, at zero and nonzero momentum, is <M(t_F) Mbar(t_0)>;
+  - the I = 2 two-pion formula D - X is half of <pi+ pi+ (t_F) (pi+ pi+)bar (t_0)> (the
+    two identical pions at each end double both diagrams), which fixes the sign of X;
+  - the isoscalar (u-bar c u + d-bar c d)/sqrt(2) gives fwd + 2 smt (the flavour weights
+    of the second term of Eq. (mesoncorr)).
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import laph, wick
+from oracle.pipeline import OraclePath
+
+
+# ---------------------------------------------------------------- exterior algebra
+def _mono_mul(a, b):
+    """Product of two monomials (sorted generator tuples): (sign, monomial) or None."""
+    if set(a) & set(b):
+        return None
+    seq = list(a) + list(b)
+    sign = 1
+    for i in range(len(seq)):              # bubble sort counting swaps
+        for j in range(len(seq) - 1 - i):
+            if seq[j] > seq[j + 1]:
+                seq[j], seq[j + 1] = seq[j + 1], seq[j]
+                sign = -sign
+    return sign, tuple(seq)
+
+
+def _mul(x, y):
+    out = {}
+    for ma, ca in x.items():
+        for mb, cb in y.items():
+            r = _mono_mul(ma, mb)
+            if r is None:
+                continue
+            s, m = r
+            out[m] = out.get(m, 0) + s * ca * cb
+    return out
+
+
+def _add(x, y, scale=1.0):
+    out = dict(x)
+    for m, c in y.items():
+        out[m] = out.get(m, 0) + scale * c
+    return out
+
+
+class Grassmann:
+    """q_j is generator j, qbar_i is generator N + i."""
+
+    def __init__(self, A):
+        self.N = A.shape[0]
+        S = {}
+        for i in range(self.N):
+            for j in range(self.N):
+                if A[i, j] != 0:
+                    S = _add(S, _mul(self.qbar(i), self.q(j)), A[i, j])
+        w, term = {(): 1.0}, {(): 1.0}
+        for k in range(1, self.N + 1):                       # e^{-S} terminates at S^N
+            term = {m: -c / k for m, c in _mul(term, S).items()}
+            w = _add(w, term)
+        self.weight = w
+        self.top = tuple(range(2 * self.N))
+        self.Z = w.get(self.top, 0)
+
+    def q(self, j):
+        return {(j,): 1.0}
+
+    def qbar(self, i):
+        return {(self.N + i,): 1.0}
+
+    def bilinear(self, M, off_bar, off_q):
+        out = {}
+        n = M.shape[0]
+        for i in range(n):
+            for j in range(n):
+                if M[i, j] != 0:
+                    out = _add(out, _mul(self.qbar(off_bar + i), self.q(off_q + j)), M[i, j])
+        return out
+
+    def expect(self, x):
+        return _mul(x, self.weight).get(self.top, 0) / self.Z
+
+
+@pytest.fixture(scope="module")
+def two_flavour():
+    rng = np.random.default_rng(4)
+    n = 2
+    A0 = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 3 * np.eye(n)
+    A = np.zeros((2 * n, 2 * n), dtype=complex)
+    A[:n, :n] = A0
+    A[n:, n:] = A0
+    return n, A0, Grassmann(A)
+
+
+def test_grassmann_two_point(two_flavour):
+    n, A0, g = two_flavour
+    inv = np.linalg.inv(A0)
+    for j in range(n):
+        for i in range(n):
+            assert abs(g.expect(_mul(g.q(j), g.qbar(i))) - inv[j, i]) < 1e-12
+            assert abs(g.expect(_mul(g.q(n + j), g.qbar(n + i))) - inv[j, i]) < 1e-12
+            assert abs(g.expect(_mul(g.q(j), g.qbar(n + i)))) < 1e-14     # flavours do not mix
+
+
+FLAV = {"u": 0, "d": 1}
+
+
+@pytest.mark.parametrize("pattern", [("uu",), ("ud",), ("uu", "uu"), ("ud", "du"), ("ud", "ud"), ("uu", "dd"),
+                                     ("ud", "du", "uu"), ("ud", "du", "ud", "du"), ("du", "du", "ud", "ud"),
+                                     ("uu", "dd", "uu", "ud")])
+def test_expect_matches_grassmann(two_flavour, pattern):
+    n, A0, g = two_flavour
+    rng = np.random.default_rng(zlib.crc32("".join(pattern).encode()))
+    Q = np.linalg.inv(A0)
+    bils, x = [], {(): 1.0}
+    for fb, f in pattern:                     # qbar flavour, q flavour
+        M = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        bils.append((M, fb, f))
+        x = _mul(x, g.bilinear(M, FLAV[fb] * n, FLAV[f] * n))
+    ref = g.expect(x)
+    got = wick.expect(bils, Q)
+    assert abs(got - ref) < 1e-10 * max(1.0, abs(ref))
+
+
+# ---------------------------------------------------------------- correlators on a lattice
+@pytest.fixture(scope="module")
+def lattice():
+    wl = synth.Workload(name="t", ns=4, nt=4, xi=3.5, csw=1.0, m0=-0.05, nv=4, gauge_seed=31, n_stout4d=3,
+                        n_stout3d=2, dil_time=(1, 0), dil_spin=(1, 0), dil_laph=(1, 0), source_times=(0,),
+                        n_noise=2)
+    path = OraclePath(wl)
+    G = path.exact_G()
+    N = wl.nt * 4 * wl.nv
+    return path, G, G.reshape(N, N)
+
+
+def _phi(path, mom):
+    if mom is None:
+        return np.broadcast_to(np.eye(path.wl.nv), (path.wl.nt, path.wl.nv, path.wl.nv))
+    return laph.mom_overlaps(path.evecs, mom)
+
+
+def _neg(mom):
+    return None if mom is None else tuple(-m for m in mom)
+
+
+@pytest.mark.parametrize("channel", ["pion", "rho", "scalar"])
+@pytest.mark.parametrize("mom", [None, (1, 0, 0)])
+def test_meson_connected_is_wick(lattice, channel, mom):
+    path, G, Q = lattice
+    nt, nv, t0 = path.wl.nt, path.wl.nv, 1
+    ph, phm = _phi(path, mom), _phi(path, _neg(mom))
+    exact = laph.exact_meson_connected(G, t0, channel, None if mom is None else ph)
+    cs = laph.channel_c(channel)
+    for dt in range(nt):
+        tf = (t0 + dt) % nt
+        w = sum(wick.correlator([(1.0, [wick.sink_bilinear(nt, nv, tf, c, ph[tf], "d", "u")])],
+                                [(1.0, [wick.source_bilinear(nt, nv, t0, c, phm[t0], "d", "u")])], Q)
+                for c in cs) / len(cs)
+        assert abs(w - exact[dt]) < 1e-10 * np.abs(exact).max()
+
+
+def test_pipi_i2_is_wick(lattice):
+    path, G, Q = lattice
+    nt, nv, t0 = path.wl.nt, path.wl.nv, 0
+    c = laph.channel_c("pion")[0]
+    one = np.eye(nv)
+    exact = laph.exact_pipi_i2(G, t0)
+    for dt in range(nt):
+        tf = (t0 + dt) % nt
+        snk = [(1.0, [wick.sink_bilinear(nt, nv, tf, c, one, "d", "u")] * 2)]
+        src = [(1.0, [wick.source_bilinear(nt, nv, t0, c, one, "d", "u")] * 2)]
+        w = wick.correlator(snk, src, Q)
+        assert abs(0.5 * w - exact[dt]) < 1e-10 * np.abs(exact).max()
+    # the crossed term matters: D alone is not the answer
+    d = laph.exact_meson_connected(G, t0, "pion") ** 2
+    assert np.abs(d - exact).max() > 1e-3 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("channel", ["pion", "scalar"])
+@pytest.mark.parametrize("mom", [None, (0, 1, 0)])
+def test_isoscalar_is_wick(lattice, channel, mom):
+    path, G, Q = lattice
+    nt, nv, t0 = path.wl.nt, path.wl.nv, 2
+    ph, phm = _phi(path, mom), _phi(path, _neg(mom))
+    c = laph.channel_c(channel)[0]
+    phi = None if mom is None else ph
+    iso = laph.isoscalar_meson(laph.exact_meson_connected(G, t0, channel, phi),
+                               laph.exact_meson_disconnected(G, t0, channel, phi))
+    r = 1.0 / np.sqrt(2.0)
+    for dt in range(nt):
+        tf = (t0 + dt) % nt
+        snk = [(r, [wick.sink_bilinear(nt, nv, tf, c, ph[tf], f, f)]) for f in "ud"]
+        src = [(r, [wick.source_bilinear(nt, nv, t0, c, phm[t0], f, f)]) for f in "ud"]
+        w = wick.correlator(snk, src, Q)
+        assert abs(w - iso[dt]) < 1e-10 * np.abs(iso).max()
