@@ -94,3 +94,46 @@ def correlator(sink_terms, source_terms, Q):
         for wr, br in source_terms:
             out += ws * wr * expect(list(bs) + list(br), Q)
     return out
+
+
+# ---------------------------------------------------------------- pions and two-pion isospin states
+# The bilinear qbar Gamma tau q transforms under isospin like tau in the adjoint; with
+# tau_+ = E_ud as the top state, lowering gives the triplet
+#     |1,+1> = u-bar d,   |1,0> = (d-bar d - u-bar u)/sqrt(2),   |1,-1> = -d-bar u,
+# as (weight, (qbar flavour, q flavour)) lists.  Two-pion states couple these with the
+# Clebsch-Gordan coefficients of 1 x 1; the first pion carries momentum p, the second -p
+# (zero total momentum, the paper's two-pion operators of Sec. V).
+_R2 = 1.0 / np.sqrt(2.0)
+PION = {+1: [(1.0, ("u", "d"))], 0: [(-_R2, ("u", "u")), (_R2, ("d", "d"))], -1: [(-1.0, ("d", "u"))]}
+
+CG_1x1 = {
+    (2, 2): [(1.0, 1, 1)],
+    (2, 1): [(_R2, 1, 0), (_R2, 0, 1)],
+    (2, 0): [(1.0 / np.sqrt(6.0), 1, -1), (2.0 / np.sqrt(6.0), 0, 0), (1.0 / np.sqrt(6.0), -1, 1)],
+    (1, 1): [(_R2, 1, 0), (-_R2, 0, 1)],
+    (1, 0): [(_R2, 1, -1), (-_R2, -1, 1)],
+    (0, 0): [(1.0 / np.sqrt(3.0), 1, -1), (-1.0 / np.sqrt(3.0), 0, 0), (1.0 / np.sqrt(3.0), -1, 1)],
+}
+
+
+def two_pion_sink(nt, nv, t, c, phi_p_t, phi_mp_t, iso):
+    """Sink operator sum_CG w pi_{m1}(p, t) pi_{m2}(-p, t) as (weight, [B1, B2]) terms."""
+    out = []
+    for w, m1, m2 in CG_1x1[iso]:
+        for w1, (fb1, f1) in PION[m1]:
+            for w2, (fb2, f2) in PION[m2]:
+                out.append((w * w1 * w2, [sink_bilinear(nt, nv, t, c, phi_p_t, fb1, f1),
+                                          sink_bilinear(nt, nv, t, c, phi_mp_t, fb2, f2)]))
+    return out
+
+
+def two_pion_source(nt, nv, t, c, phi_p_t, phi_mp_t, iso):
+    """Source partner of two_pion_sink: every bilinear replaced by its source partner
+    (Phi_{-p} for the pion of momentum p) and every weight conjugated."""
+    out = []
+    for w, m1, m2 in CG_1x1[iso]:
+        for w1, (fb1, f1) in PION[m1]:
+            for w2, (fb2, f2) in PION[m2]:
+                out.append((np.conj(w * w1 * w2), [source_bilinear(nt, nv, t, c, phi_mp_t, fb1, f1),
+                                                   source_bilinear(nt, nv, t, c, phi_p_t, fb2, f2)]))
+    return out

@@ -11,7 +11,11 @@ and flavour weights of the oracle's correlator formulas.
   - the I = 2 two-pion formula D - X is half of <pi+ pi+ (t_F) (pi+ pi+)bar (t_0)> (the
     two identical pions at each end double both diagrams), which fixes the sign of X;
   - the isoscalar (u-bar c u + d-bar c d)/sqrt(2) gives fwd + 2 smt (the flavour weights
-    of the second term of Eq. (mesoncorr)).
+    of the second term of Eq. (mesoncorr));
+  - the two-pion isospin operators (pion triplet coupled by the Clebsch-Gordan
+    coefficients of 1 x 1, momenta p and -p): all members of each multiplet have equal
+    correlators, different isospins do not correlate, I = 1 vanishes at p = 0 and the
+    I = 2 top state is twice D - X.
 """
 import zlib
 
@@ -207,3 +211,35 @@ def test_isoscalar_is_wick(lattice, channel, mom):
         src = [(r, [wick.source_bilinear(nt, nv, t0, c, phm[t0], f, f)]) for f in "ud"]
         w = wick.correlator(snk, src, Q)
         assert abs(w - iso[dt]) < 1e-10 * np.abs(iso).max()
+
+
+def _pipi(path, Q, tf, t0, snk_iso, src_iso, mom):
+    nt, nv = path.wl.nt, path.wl.nv
+    c = laph.channel_c("pion")[0]
+    ph, phm = _phi(path, mom), _phi(path, _neg(mom))
+    return wick.correlator(wick.two_pion_sink(nt, nv, tf, c, ph[tf], phm[tf], snk_iso),
+                           wick.two_pion_source(nt, nv, t0, c, ph[t0], phm[t0], src_iso), Q)
+
+
+@pytest.mark.parametrize("mom", [None, (1, 0, 0)])
+def test_two_pion_isospin_multiplets(lattice, mom):
+    """Degenerate u, d: every member of an isospin multiplet has the same correlator on each
+    configuration, and operators of different isospin do not correlate."""
+    path, G, Q = lattice
+    t0 = 1
+    for dt in (0, 1, 2):
+        tf = (t0 + dt) % path.wl.nt
+        c = {k: _pipi(path, Q, tf, t0, k, k, mom) for k in [(2, 2), (2, 1), (2, 0), (1, 1), (1, 0), (0, 0)]}
+        scale = max(abs(v) for v in c.values())
+        assert abs(c[(2, 1)] - c[(2, 2)]) < 1e-10 * scale and abs(c[(2, 0)] - c[(2, 2)]) < 1e-10 * scale
+        assert abs(c[(1, 0)] - c[(1, 1)]) < 1e-10 * scale
+        assert abs(c[(0, 0)] - c[(2, 2)]) > 1e-3 * scale          # I = 0 and I = 2 differ
+        for a, b in [((2, 0), (0, 0)), ((0, 0), (2, 0)), ((1, 0), (0, 0)), ((2, 0), (1, 0))]:
+            assert abs(_pipi(path, Q, tf, t0, a, b, mom)) < 1e-10 * scale
+        if mom is None:
+            # equal momenta: the isospin-antisymmetric operator vanishes identically
+            assert abs(c[(1, 0)]) < 1e-12 * scale
+            # the I = 2 top state doubles the D - X of exact_pipi_i2
+            assert abs(c[(2, 2)] - 2.0 * laph.exact_pipi_i2(G, t0)[dt]) < 1e-10 * scale
+        else:
+            assert abs(c[(1, 0)]) > 1e-3 * scale
