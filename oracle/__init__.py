@@ -23,6 +23,7 @@ Modules:
   dilution   time/spin/LapH dilution projectors
   dirac      anisotropic Wilson-clover matrix K, BiCGStab, dense solves
   laph       sources, sinks, meson functions and correlators (momentum, same-time lines)
+  displacement  gauge-covariant displacements, displaced LapH overlaps and meson functions
   wick       Wick's theorem for products of LapH bilinears (brute-force correlators)
   precond    gauge-covariant learned preconditioner (forward/backward)
 """
