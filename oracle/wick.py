@@ -137,3 +137,71 @@ def two_pion_source(nt, nv, t, c, phi_p_t, phi_mp_t, iso):
                 out.append((np.conj(w * w1 * w2), [source_bilinear(nt, nv, t, c, phi_mp_t, fb1, f1),
                                                    source_bilinear(nt, nv, t, c, phi_p_t, fb2, f2)]))
     return out
+
+
+# ---------------------------------------------------------------- stochastic estimation (Sec. II-III)
+# The stochastic LapH method replaces every quark line of a diagram by a noisy estimate
+# built from one noise: with phi^[b] = G P^(b) rho (the sink coefficients of the solves)
+# and rho^[b] = P^(b) rho, Q_hat = sum_b phi^[b] rho^[b]dag, whose noise average is G on the
+# columns the projectors cover (Z_N noise, Sec. II).  The graphical rules of Sec. III then
+# read, term by term of the Wick expansion above:
+#   * a line leaving the source time t0 (qbar at t0) uses a forward line sourced at t0;
+#   * a line from the sink time tF back to t0 uses a forward line through gamma_5
+#     Hermiticity, Q(t0 <- tF) = Gamma' Q(tF <- t0)^dag Gamma', Gamma' = gamma_4 gamma_5
+#     (which follows from K^dag = gamma_5 K gamma_5 and Omega = gamma_4 K);
+#   * a line from tF to tF uses a same-time line (time interlacing, every projector solved);
+#   * the lines of one term all carry different noises: propagators take the next unused
+#     line of their kind in the order the term's cycles visit them.
+
+def line_estimate(coef: np.ndarray, rho_b: np.ndarray) -> np.ndarray:
+    """Q_hat = sum_b phi^[b] rho^[b]dag over the full LapH space; coef, rho_b [nb][nt][4][nv]."""
+    nb = coef.shape[0]
+    return coef.reshape(nb, -1).T @ np.conj(rho_b.reshape(nb, -1))
+
+
+def gamma_swap(q_hat: np.ndarray, nt: int, nv: int, gamma_prime: np.ndarray) -> np.ndarray:
+    """Gamma' Q_hat^dag Gamma' with Gamma' acting on the spin index of (t, alpha, n)."""
+    g = np.kron(np.eye(nt), np.kron(gamma_prime, np.eye(nv)))
+    return g @ q_hat.conj().T @ g
+
+
+def stochastic_expect(bilinears, times, t0, fwd, bwd, smt):
+    """< B_1 ... B_m > with every propagator of every Wick term replaced by a line estimate:
+    fwd[i] (lines from t0), bwd[i] (the gamma_5-swapped forward lines, tF -> t0), smt[i]
+    (same-time lines at tF); times[k] is the time slice of bilinear k."""
+    m = len(bilinears)
+    total = 0.0 + 0.0j
+    for perm in itertools.permutations(range(m)):
+        if any(bilinears[k][2] != bilinears[perm[k]][1] for k in range(m)):
+            continue
+        used = {"f": 0, "s": 0}
+        term = 1.0 + 0.0j
+        for cyc in _cycles(perm):
+            prod = None
+            for k in cyc:
+                # Q(j_k, i_perm[k]): from qbar of B_perm[k] (its time) to q of B_k
+                t_src, t_snk = times[perm[k]], times[k]
+                if t_src == t0:
+                    q = fwd[used["f"]]
+                    used["f"] += 1
+                elif t_snk == t0:
+                    q = bwd[used["f"]]
+                    used["f"] += 1
+                else:
+                    q = smt[used["s"]]
+                    used["s"] += 1
+                f = bilinears[k][0] @ q
+                prod = f if prod is None else prod @ f
+            term *= np.trace(prod)
+        total += _sign(perm) * term
+    return (-1) ** m * total
+
+
+def stochastic_correlator(sink_terms, source_terms, tF, t0, fwd, bwd, smt):
+    """Stochastic estimate of < O_sink(tF) O_source(t0) > (see stochastic_expect)."""
+    out = 0.0 + 0.0j
+    for ws, bs in sink_terms:
+        for wr, br in source_terms:
+            times = [tF] * len(bs) + [t0] * len(br)
+            out += ws * wr * stochastic_expect(list(bs) + list(br), times, t0, fwd, bwd, smt)
+    return out
