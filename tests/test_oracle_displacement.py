@@ -26,7 +26,6 @@ import pytest
 import synth
 from oracle import displacement as dsp
 from oracle import gauge, laph, laplacian, wick
-from oracle.pipeline import OraclePath
 
 PATHS = [(1, 1, 1), (-2,), (3, -1), (2, 2, -3)]
 
@@ -90,10 +89,8 @@ def test_empty_paths_and_gauge_invariance(links):
 
 
 @pytest.fixture(scope="module")
-def free_shell():
-    evals, v = laplacian.lowest_eigpairs(unit_links(6, 1), 22)
-    assert abs(evals[0, 20] - 1.0) < 1e-10 and abs(evals[0, 21] - 2.0) < 1e-10
-    return v[:, :21]
+def free_shell(free_shell_6):
+    return free_shell_6
 
 
 @pytest.mark.parametrize("pb,p", [((), (1, 1, 1)), ((), (1,)), ((2,), (-2,)), ((3, 3), ()), ((1, 2), (1, 2))])
@@ -106,12 +103,8 @@ def test_free_field_displaced_trace(free_shell, pb, p):
 
 
 @pytest.fixture(scope="module")
-def full():
-    wl = synth.Workload(name="t", ns=4, nt=4, xi=3.5, csw=1.0, m0=-0.05, nv=4, gauge_seed=31, n_stout4d=3,
-                        n_stout3d=2, dil_time=(1, 0), dil_spin=(1, 0), dil_laph=(1, 0), source_times=(0,),
-                        n_noise=2)
-    path = OraclePath(wl)
-    return path, path.exact_G()
+def full(exact_4x4):
+    return exact_4x4
 
 
 @pytest.mark.parametrize("c_name", ["pion", "rho"])

@@ -21,21 +21,14 @@ from oracle import gauge, laph
 from oracle.pipeline import OraclePath
 
 
-def _wl():
-    return synth.Workload(name="t", ns=4, nt=4, xi=3.5, csw=1.0, m0=-0.05, nv=4, gauge_seed=31, n_stout4d=3,
-                          n_stout3d=2, dil_time=(1, 0), dil_spin=(1, 0), dil_laph=(1, 0), source_times=(0,),
-                          n_noise=2)
-
-
 def all_projectors(path):
     nT, nS, nL = dl.counts(path.dil, path.wl.nt, path.wl.nv)
     return list(range(nT * nS * nL))
 
 
 @pytest.fixture(scope="module")
-def full():
-    path = OraclePath(_wl())
-    G = path.exact_G()
+def full(exact_4x4):
+    path, G = exact_4x4
     bs = all_projectors(path)
     lines = [path.line(s, bs, method="lu")[0] for s in (3, 4)]
     return path, G, lines

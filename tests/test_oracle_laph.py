@@ -18,19 +18,9 @@ from oracle import dilution as dl
 from oracle.pipeline import OraclePath
 
 
-def _wl(**kw):
-    base = dict(name="t", ns=4, nt=4, xi=3.5, csw=1.0, m0=-0.05, nv=4, gauge_seed=31,
-                n_stout4d=3, n_stout3d=2, dil_time=(1, 0), dil_spin=(1, 0), dil_laph=(1, 0),
-                source_times=(0,), n_noise=2)
-    base.update(kw)
-    return synth.Workload(**base)
-
-
 @pytest.fixture(scope="module")
-def full():
-    path = OraclePath(_wl())
-    G = path.exact_G()
-    return path, G
+def full(exact_4x4):
+    return exact_4x4
 
 
 def test_full_dilution_single_line_is_exact(full):

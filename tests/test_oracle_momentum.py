@@ -22,7 +22,6 @@ import pytest
 
 import synth
 from oracle import gauge, laph, laplacian
-from oracle.pipeline import OraclePath
 
 
 def unit_links(ns, nt):
@@ -37,11 +36,8 @@ def test_zero_momentum_overlap_is_identity():
 
 
 @pytest.fixture(scope="module")
-def free_shell():
-    evals, v = laplacian.lowest_eigpairs(unit_links(6, 1), 22)
-    # eigenvalues 21 and 22 are 4 sin^2(pi/6) = 1 and 2: the lowest 21 form a closed shell
-    assert abs(evals[0, 20] - 1.0) < 1e-10 and abs(evals[0, 21] - 2.0) < 1e-10
-    return v[:, :21]
+def free_shell(free_shell_6):
+    return free_shell_6
 
 
 @pytest.mark.parametrize("mom,pairs", [((0, 0, 0), 7), ((1, 0, 0), 2), ((0, 1, 1), 2), ((0, 0, 2), 1),
@@ -80,12 +76,8 @@ def test_translation_phase(shifted_pair, shift, mom):
 
 
 @pytest.fixture(scope="module")
-def full():
-    wl = synth.Workload(name="t", ns=4, nt=4, xi=3.5, csw=1.0, m0=-0.05, nv=4, gauge_seed=31, n_stout4d=3,
-                        n_stout3d=2, dil_time=(1, 0), dil_spin=(1, 0), dil_laph=(1, 0), source_times=(0,),
-                        n_noise=2)
-    path = OraclePath(wl)
-    return path, path.exact_G()
+def full(exact_4x4):
+    return exact_4x4
 
 
 @pytest.mark.parametrize("channel", ["pion", "rho", "scalar"])

@@ -14,18 +14,10 @@ noisy quark lines joined by the graphical rules; oracle/wick.py stochastic_expec
 import numpy as np
 import pytest
 
-import synth
 from oracle import dilution as dl
 from oracle import laph, wick
-from oracle.pipeline import OraclePath
 
 GP = laph.GAMMA[3] @ laph.GAMMA5
-
-
-def _wl():
-    return synth.Workload(name="t", ns=4, nt=4, xi=3.5, csw=1.0, m0=-0.05, nv=4, gauge_seed=31, n_stout4d=3,
-                          n_stout3d=2, dil_time=(1, 0), dil_spin=(1, 0), dil_laph=(1, 0), source_times=(0,),
-                          n_noise=2)
 
 
 def estimate(path, noise_id, dil, bs):
@@ -62,9 +54,8 @@ def line_sets(path, t0, dil_fwd, dil_smt, seed):
 
 
 @pytest.fixture(scope="module")
-def setup():
-    path = OraclePath(_wl())
-    G = path.exact_G()
+def setup(exact_4x4):
+    path, G = exact_4x4
     N = path.wl.nt * 4 * path.wl.nv
     return path, G, G.reshape(N, N)
 

@@ -22,9 +22,7 @@ import zlib
 import numpy as np
 import pytest
 
-import synth
 from oracle import laph, wick
-from oracle.pipeline import OraclePath
 
 
 # ---------------------------------------------------------------- exterior algebra
@@ -141,13 +139,9 @@ def test_expect_matches_grassmann(two_flavour, pattern):
 
 # ---------------------------------------------------------------- correlators on a lattice
 @pytest.fixture(scope="module")
-def lattice():
-    wl = synth.Workload(name="t", ns=4, nt=4, xi=3.5, csw=1.0, m0=-0.05, nv=4, gauge_seed=31, n_stout4d=3,
-                        n_stout3d=2, dil_time=(1, 0), dil_spin=(1, 0), dil_laph=(1, 0), source_times=(0,),
-                        n_noise=2)
-    path = OraclePath(wl)
-    G = path.exact_G()
-    N = wl.nt * 4 * wl.nv
+def lattice(exact_4x4):
+    path, G = exact_4x4
+    N = path.wl.nt * 4 * path.wl.nv
     return path, G, G.reshape(N, N)
 
 
