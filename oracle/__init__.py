@@ -24,6 +24,7 @@ Modules:
   dirac      anisotropic Wilson-clover matrix K, BiCGStab, dense solves
   laph       sources, sinks, meson functions and correlators (momentum, same-time lines)
   displacement  gauge-covariant displacements, displaced LapH overlaps and meson functions
+  baryon     baryon functions and correlators (three-quark elementals, LapH tensor)
   wick       Wick's theorem for products of LapH bilinears (brute-force correlators)
   precond    gauge-covariant learned preconditioner (forward/backward)
 """
