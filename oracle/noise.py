@@ -57,3 +57,47 @@ def z4_codes(nt: int, nv: int, noise_id: int, config_id: int) -> np.ndarray:
 
 def z4_values(codes: np.ndarray) -> np.ndarray:
     return (1j) ** codes.astype(np.int64)
+
+
+# ---------------------------------------------------------------- the paper's generator (oracle only)
+# Sec. IV draws the Z4 elements from the Mersenne twister, two bits at a time in a fixed
+# order.  Written from its published definition (Matsumoto and Nishimura, ACM TOMACS 8, 1998):
+# MT19937 with the 1998/2002 seeding rule init_genrand.  Reading taken for the parts the paper
+# leaves open: the generator is seeded with m = (k << 16) | s; element idx = (t*4 + alpha)*N_v + n
+# takes bits 2j, 2j+1 (j = idx mod 16) of output word idx // 16, least significant pair first.
+# The GPU path keeps the counter-based generator above; this mode exists for fidelity checks.
+
+_MT_N, _MT_M = 624, 397
+
+
+def mt19937_words(seed: int, count: int) -> np.ndarray:
+    """The first `count` 32-bit outputs of MT19937 seeded by init_genrand(seed)."""
+    mt = [0] * _MT_N
+    mt[0] = seed & 0xFFFFFFFF
+    for i in range(1, _MT_N):
+        mt[i] = (1812433253 * (mt[i - 1] ^ (mt[i - 1] >> 30)) + i) & 0xFFFFFFFF
+    out = []
+    idx = _MT_N
+    while len(out) < count:
+        if idx >= _MT_N:
+            for i in range(_MT_N):
+                y = (mt[i] & 0x80000000) | (mt[(i + 1) % _MT_N] & 0x7FFFFFFF)
+                mt[i] = mt[(i + _MT_M) % _MT_N] ^ (y >> 1) ^ (0x9908B0DF if y & 1 else 0)
+            idx = 0
+        y = mt[idx]
+        idx += 1
+        y ^= y >> 11
+        y ^= (y << 7) & 0x9D2C5680
+        y ^= (y << 15) & 0xEFC60000
+        y ^= y >> 18
+        out.append(y & 0xFFFFFFFF)
+    return np.array(out, dtype=np.uint64)
+
+
+def z4_codes_mt(nt: int, nv: int, noise_id: int, config_id: int) -> np.ndarray:
+    """uint8 codes v[t, alpha, n] from MT19937 two bits at a time (the paper's generator)."""
+    n = nt * 4 * nv
+    words = mt19937_words(noise_seed(noise_id, config_id), (n + 15) // 16)
+    idx = np.arange(n, dtype=np.uint64)
+    codes = (words[idx // np.uint64(16)] >> (np.uint64(2) * (idx % np.uint64(16)))) & np.uint64(3)
+    return codes.astype(np.uint8).reshape(nt, 4, nv)

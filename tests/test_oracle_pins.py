@@ -333,3 +333,27 @@ def test_inversion_counts_match_the_paper():
         n = n_time * nS * nL
         assert n == c["inversions"], c["what"]
         per.append(n)
+
+
+def test_mt19937_known_value_and_z4_extraction():
+    """The paper's generator (Sec. IV: Mersenne twister, two bits per Z4 element), oracle only:
+    MT19937 against the value fixed by the C++ standard (tests/golden/mt19937.json) and against
+    numpy's MT19937 bit generator with the same legacy seeding; Z4 codes take the two-bit
+    fields of each word least significant first."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    gold = json.load(open(os.path.join(here, "golden", "mt19937.json")))
+    w = noise.mt19937_words(gold["seed"], gold["index"])
+    assert int(w[-1]) == gold["value"]
+    bg = np.random.MT19937()
+    if hasattr(bg, "_legacy_seeding"):                 # numpy's init_genrand path
+        bg._legacy_seeding(123456789)
+        assert np.array_equal(noise.mt19937_words(123456789, 1300), bg.random_raw(1300).astype(np.uint64))
+    codes = noise.z4_codes_mt(4, 8, 3, 7)
+    words = noise.mt19937_words(noise.noise_seed(3, 7), 8)
+    flat = codes.ravel()
+    for idx in (0, 1, 15, 16, 77, 127):
+        assert flat[idx] == (int(words[idx // 16]) >> (2 * (idx % 16))) & 3
+    big = noise.z4_codes_mt(64, 64, 1, 1).ravel()
+    counts = np.bincount(big, minlength=4)
+    expected = big.size / 4
+    assert np.sum((counts - expected) ** 2 / expected) < 20.0          # chi^2 with 3 dof, far tail
