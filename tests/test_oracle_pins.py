@@ -111,6 +111,37 @@ def test_clover_abelian_closed_form():
     assert np.abs(f - expect).max() < 1e-14
 
 
+@pytest.mark.parametrize("mu,nu", list(itertools.combinations(range(4), 2)))
+def test_clover_plane_weight_spectrum(mu, nu):
+    """The clover term's weight per plane, from the spectrum of the site matrix A(x).
+
+    An abelian, colour-diagonal field confined to the (mu, nu) plane, U_mu(x) = exp(i a x_nu h)
+    with h = diag(1, -1, 0), has F_{mu nu} = -sin(a) h on every site (the closed form of the test
+    above, any plane) and F = 0 in the five other planes.  sigma_{mu nu} squares to 1 with
+    eigenvalues +1, +1, -1, -1, so A = (m0 + sum_mu w_mu) - (c_sw/2) w_{mu nu} sigma_{mu nu} F_{mu nu}
+    has eigenvalues c0 and c0 +- (c_sw/2) w_{mu nu} sin(a), four times each.  The weight is
+    (1 + 1/xi)/2 for the planes with the time direction and 1/xi for the spatial ones: a swap
+    of the two, or one weight for every plane, moves the spread and fails here."""
+    from oracle.dirac import diag_matrix
+    ns = nt = 4
+    a, xi, m0, csw = 2 * np.pi / 4, 3.5, -0.07, 1.3
+    u = np.broadcast_to(np.eye(3), (nt, ns, ns, ns, 4, 3, 3)).astype(complex).copy()
+    h = np.array([1.0, -1.0, 0.0])
+    axis = {0: 3, 1: 2, 2: 1, 3: 0}[nu]          # array axis of coordinate x_nu ([t, z, y, x])
+    for c in range(ns):
+        sl = [slice(None)] * 4
+        sl[axis] = c
+        u[tuple(sl) + (mu,)] = np.diag(np.exp(1j * a * c * h))
+    A = diag_matrix(u, m0, csw, xi)
+    c0 = m0 + 3.0 / xi + 1.0
+    w = 0.5 * (1.0 + 1.0 / xi) if nu == 3 else 1.0 / xi
+    d = 0.5 * csw * w * np.sin(a)
+    expect = np.sort(np.repeat([c0 - d, c0, c0 + d], 4))
+    for site in [(0, 0, 0, 0), (1, 2, 3, 0), (3, 1, 0, 2)]:
+        ev = np.linalg.eigvalsh(A[site])
+        assert np.abs(np.sort(ev) - expect).max() < 1e-13, (mu, nu, ev, expect)
+
+
 # ---------------------------------------------------------------- Laplacian
 def test_free_laplacian_spectrum():
     ns = 4
