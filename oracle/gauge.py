@@ -69,6 +69,20 @@ def prepare_links(u0: np.ndarray, rho: float, n4d: int, n3d: int):
     return u, ut
 
 
+def prepare_links_window(u0: np.ndarray, t0: int, halo: int, rho: float, n4d: int, n3d: int):
+    """prepare_links on the time slices t0-halo .. t0+halo of u0 (periodic indices of the full
+    lattice), smeared as a periodic lattice of 2 halo + 1 slices.
+
+    A stout step (Sec. II recipe) updates each link from its staples, which reach one slice
+    forward and back, so the error from closing the window on itself spreads inwards by one
+    slice per 4D step; 3D steps do not spread in time.  Slices t0 - (halo - n4d) .. t0 + (halo -
+    n4d) of the window (positions n4d .. 2 halo - n4d) therefore equal those of the full
+    lattice's smearing exactly.  Returns (u, ut) of the window, slice t0 at position halo."""
+    nt = u0.shape[0]
+    idx = [(t0 + k) % nt for k in range(-halo, halo + 1)]
+    return prepare_links(np.ascontiguousarray(u0[idx]), rho, n4d, n3d)
+
+
 def plaquette(u: np.ndarray, mu: int, nu: int) -> np.ndarray:
     """P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag."""
     umu, unu = u[..., mu, :, :], u[..., nu, :, :]

@@ -6,21 +6,27 @@
 // processes whose device memory is fully reserved up front, or real-time
 // loops where an allocation would stall or break a capture.  This entry
 // point therefore allocates nothing.  Its scratch (meson-function matrices,
-// the diluted noise at t0, the projector masks, the list of projectors) lives
+// the diluted noise at t0, the projector masks) lives
 // in one file-scope __device__ array of fixed size, which every GPU that loads
 // the library holds until the process exits.  The caller passes inputs and
 // outputs as device pointers; host pointers are rejected because staging
 // them would need an allocation.
 //
-// The array's address is looked up once per device (cudaGetSymbolAddress with
-// that device current) on the first call made on that device; make that first
-// call before any stream capture.  Every call shares the array and leaves the
-// last call's contents in it, so calls that overlap on the GPU (different
-// streams or threads without ordering) race on it.
+// Every call runs on the device that holds its arrays: it reads that device
+// from the output pointer, requires every input (and a non-default stream) to
+// belong to the same device, makes it current for the call and restores the
+// caller's current device on return.  With that device current it looks up the
+// array's address (cudaGetSymbolAddress) on every call, so the address stays
+// right after a device reset.  The first call on a device also loads the
+// library's kernels there; make that first call before any stream capture.
+// The projector list travels to the device inside a kernel argument (at most
+// NA_MAX_NB entries), not through a copy from the caller's host array.  Every
+// call shares the array and leaves the last call's contents in it, so calls
+// that overlap on the GPU (different streams or threads without ordering) race
+// on it.
 //
 // The contraction kernels are the ones of correlate() (correlate.cu); only the
 // origin of the scratch memory differs.
-#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -53,13 +59,20 @@ __device__ __forceinline__ bool na_proj(int type, int J, int N, int b, int i) {
     }
 }
 
-__global__ void na_mask_kernel(int nt, int nv, int nb, laph_dilution d, int nS, int nL, const int *blist,
+// The projector list by value (a kernel argument of 2 KB): no host-to-device copy of the
+// caller's array is needed.
+constexpr int NA_MAX_NB = 512;
+struct NaBlist {
+    int b[NA_MAX_NB];
+};
+
+__global__ void na_mask_kernel(int nt, int nv, int nb, laph_dilution d, int nS, int nL, NaBlist blist,
                                uint8_t *mask) {
     int w = nt + 4 + nv;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nb * w) return;
     int i = idx / w, e = idx % w;
-    int b = blist[i];
+    int b = blist.b[i];
     int bL = b % nL, bS = (b / nL) % nS, bT = b / (nL * nS);
     bool v;
     if (e < nt) v = na_proj(d.T.type, d.T.J, nt, bT, e);
@@ -122,27 +135,42 @@ static W4 na_weight(const NaMat &c, double s) {
     return w;
 }
 
-// Per-device address of the scratch array, looked up on the first call on that device.
-static std::mutex g_na_mu;
-static void *g_na_addr[256];
-
+// Device address of the scratch array on the current device.  Looked up on every call (cheap
+// once the module is loaded on that device), so no address outlives a device reset.
 static unsigned char *scratch_for_current_device() {
-    int dev = 0;
-    LAPH_CUDA(cudaGetDevice(&dev));
-    LAPH_REQUIRE(dev >= 0 && dev < 256, "device index out of range");
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            throw Error(LAPH_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array failed: ") +
-                                           cudaGetErrorString(e));
-        }
-        g_na_addr[dev] = p;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        throw Error(LAPH_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array failed: ") +
+                                       cudaGetErrorString(e));
     }
-    return (unsigned char *)g_na_addr[dev];
+    return (unsigned char *)p;
 }
+
+// Device that owns a device (or managed) allocation; -1 for host memory or an unknown pointer.
+static int na_device_of(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return -1;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? a.device : -1;
+}
+
+// Makes `dev` current for the lifetime of the object and restores the previous device after.
+struct NaDeviceScope {
+    int prev = -1;
+    explicit NaDeviceScope(int dev) {
+        LAPH_CUDA(cudaGetDevice(&prev));
+        if (prev != dev) LAPH_CUDA(cudaSetDevice(dev));
+    }
+    ~NaDeviceScope() {
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != prev) (void)cudaSetDevice(prev);
+    }
+};
 
 // Bump allocator over the fixed array (256-byte aligned pieces).
 struct Carve {
@@ -157,11 +185,14 @@ struct Carve {
     }
 };
 
+// Scratch of one call: projector masks, the diluted noise of every line at t0, one sink /
+// source meson-function pair for a meson channel (the rho components reuse it in turn), and
+// for I=2 pi pi two pairs plus the crossed-term matrices.
 static size_t na_bytes(int nt, int nv, int nb, int nlines, bool pipi) {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    size_t s = al(sizeof(int) * nb) + al((size_t)nb * (nt + 4 + nv));
+    size_t s = al((size_t)nb * (nt + 4 + nv));
     s += nlines * al(sizeof(c64) * nb * 4 * nv);
-    s += 2 * (al(sizeof(c64) * nt * nb * nb) + al(sizeof(c64) * nb * nb));
+    s += (pipi ? 2 : 1) * (al(sizeof(c64) * nt * nb * nb) + al(sizeof(c64) * nb * nb));
     if (pipi) s += 3 * al(sizeof(c64) * nt * nb * nb) + 2 * al(sizeof(c64) * nb * nb) + 2 * al(sizeof(c64) * nt);
     return s;
 }
@@ -193,16 +224,32 @@ extern "C" int correlate_noalloc(const laph_lattice *lat, const laph_corr_spec *
                                           " bytes of scratch, above the fixed " +
                                           std::to_string(NOALLOC_SCRATCH_BYTES) +
                                           "-byte array; use correlate() or fewer projectors");
-        for (int k = 0; k < nlines; ++k)
-            LAPH_REQUIRE(coef[k] && noise[k] && is_device_ptr(coef[k]) && is_device_ptr(noise[k]),
+        LAPH_REQUIRE(nb <= NA_MAX_NB, "correlate_noalloc takes at most " + std::to_string(NA_MAX_NB) +
+                                          " projectors per line");
+        // every array on one device, which runs the call
+        const int dev = na_device_of(corr);
+        LAPH_REQUIRE(dev >= 0, "correlate_noalloc takes a device output pointer");
+        for (int k = 0; k < nlines; ++k) {
+            LAPH_REQUIRE(coef[k] && noise[k], "null line array");
+            const int dc = na_device_of(coef[k]), dn = na_device_of(noise[k]);
+            LAPH_REQUIRE(dc >= 0 && dn >= 0,
                          "correlate_noalloc takes device pointers only (host arrays would need staging)");
-        LAPH_REQUIRE(is_device_ptr(corr), "correlate_noalloc takes a device output pointer");
+            LAPH_REQUIRE(dc == dev && dn == dev, "correlate_noalloc: the line arrays and the output must be on one "
+                                                 "device");
+        }
         cudaStream_t s = as_stream(stream);
+        // the legacy (0), legacy-handle (1) and per-thread (2) default streams follow the current device
+        if (reinterpret_cast<uintptr_t>(s) > 2) {
+            int sdev = -1;
+            LAPH_CUDA(cudaStreamGetDevice(s, &sdev));
+            LAPH_REQUIRE(sdev == dev, "correlate_noalloc: the stream belongs to another device than the arrays");
+        }
+        NaDeviceScope scope(dev);
+        NaBlist bl;
+        for (int i = 0; i < nb; ++i) bl.b[i] = spec->b_list[i];
         Carve cv{scratch_for_current_device()};
-        int *dblist = cv.take<int>(nb);
         uint8_t *mask = cv.take<uint8_t>((size_t)nb * (nt + 4 + nv));
-        LAPH_CUDA(cudaMemcpyAsync(dblist, spec->b_list, sizeof(int) * nb, cudaMemcpyHostToDevice, s));
-        na_mask_kernel<<<grid_for((long)nb * (nt + 4 + nv), 256), 256, 0, s>>>(nt, nv, nb, spec->dil, nS, nL, dblist,
+        na_mask_kernel<<<grid_for((long)nb * (nt + 4 + nv), 256), 256, 0, s>>>(nt, nv, nb, spec->dil, nS, nL, bl,
                                                                               mask);
         LAPH_LAUNCH_CHECK();
         std::vector<c64 *> rho(nlines);

@@ -64,3 +64,24 @@ def test_eigvecs_medium_sampled_slices():
     sub = ut[slices]
     ev_o, vec_o = laplacian.lowest_eigpairs(sub, wl.nv, "sparse")
     _check(sub, wl.nv, host(evals), host(evecs), ev_o, vec_o, slices)
+
+
+@pytest.mark.parametrize("nv", [3, 21])
+def test_eigvecs_free_field_degenerate_shells(nv):
+    """U = 1 on 4^3: the spectrum of -Delta is sum_k 4 sin^2(pi n_k / 4) with every level at
+    least three-fold (colour) degenerate: 0 (x3), 2 (x18), 4 (x45), ...  N_v = 3 and 21 end on
+    a shell boundary, so the wanted eigenspace is unique although single vectors are not; the
+    eigenvalues must meet the closed form and the eigenprojector the oracle's dense one."""
+    import torch
+    L = lib()
+    ns, nt = 4, 2
+    u = np.broadcast_to(np.eye(3, dtype=complex), (nt, ns, ns, ns, 4, 3, 3)).copy()
+    ev_o, vec_o = laplacian.lowest_eigpairs(u, nv, "dense")
+    exact = np.sort(np.array([0.0] * 3 + [2.0] * 18))[:nv]
+    assert np.abs(ev_o - exact[None]).max() < 1e-12
+    evals = empty((nt, nv), torch.float64)
+    evecs = empty((nt, nv, ns ** 3, 3), torch.complex128)
+    rep = L.laph_eigvecs(context(), L.lattice(ns, nt, 3.5), dev(u), nv, evals, evecs)
+    assert rep.nconv == nv
+    assert np.abs(host(evals) - exact[None]).max() <= 1e-10 * 2.0
+    assert laplacian.eigenprojector_distance(host(evecs), vec_o) <= 1e-8

@@ -1,0 +1,112 @@
+"""Parity at the paper-shaped size: 24^3 x 128, xi = 3.5, N_v = 64, (TI16, SF, LI8), in the
+launch configuration the benchmark times (one block of the 32 diluted sources of one
+time-interlace projector, b_T = 0, of one noise, solved in one 32-RHS launch).  The oracle
+cannot smear the 1.8 M-site field inside a test, so it smears the 23 slices around a sampled
+slice (oracle.gauge.prepare_links_window, exact on the central three slices, pinned in
+tests/test_oracle_window.py) and every check is made on that slice:
+
+  eigenpairs (a1)   slice 48 against scipy's eigsh at N_v = 64     eigenvalues rel <= 1e-10,
+                                                                   eigenprojector <= 1e-8
+  noise (a2)        the whole Z4 code table against the oracle's Philox     bit for bit
+  sources (a2)      V^dag gamma_4 y_b on slice 48 equals P^(b) rho          <= 1e-12
+  solves (a3)       for every source, slice 48 of the FP64 true residual y - K x under the
+                    oracle's plain-C K on the oracle's links       <= 1e-10 ||y||
+  sinks (a4)        sampled coefficients on slice 48 equal sum_x conj(V) x  rel <= 1e-12
+
+Slice 48 carries the sources of b_T = 0 (TI16 puts them on slices 0, 16, 32, ...)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dilution as dl
+from oracle import gauge, laplacian
+from oracle import noise as onoise
+from oracle.dirac import WilsonClover
+from oracle.fast import FastK
+from oracle.gamma import GAMMA
+from tests.gpu_util import host, lib, requires_gpu
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+TS = 48        # sampled slice
+HALO = 11      # 10 4D stout steps + one slice for the stencil
+BLOCK = 32     # right-hand sides per solver launch (the benchmark's block)
+
+
+@pytest.fixture(scope="module")
+def paper():
+    import torch
+    L = lib()
+    from paper_1104_3870_gb300.pipeline import LapHPath, LatticeSpec, projectors_for_time
+    wl = synth.WORKLOADS["paper_24x128"]
+    spec = LatticeSpec(wl.ns, wl.nt, wl.xi, wl.m0, wl.csw, wl.nv, (wl.dil_time, wl.dil_spin, wl.dil_laph),
+                       wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
+    u0 = wl.gauge()
+    path = LapHPath(spec)
+    u, ut = path.prepare_links(u0)
+    evals, evecs, rep = path.eigvecs(ut)
+    bs = projectors_for_time(spec, 0)
+    assert len(bs) == BLOCK
+    rhs, codes = path.sources(evecs, 0, wl.config_id, bs)
+    sol, reps = path.solve(u, rhs, mode=L.MIXED_FP32, rhs_block=BLOCK)
+    coef = path.sinks(evecs, sol)
+    torch.cuda.synchronize()
+    bnorm = torch.linalg.vector_norm(rhs.reshape(BLOCK, -1), dim=1).cpu().numpy()
+    out = dict(wl=wl, spec=spec, bs=bs, rep=rep, reps=reps, bnorm=bnorm,
+               evals=host(evals), evecs=host(evecs[TS]), codes=host(codes),
+               rhs=host(rhs[:, TS]), sol=host(sol[:, TS - 1:TS + 2]), coef=host(coef[:, TS]))
+    del rhs, sol, coef, evecs, u, ut
+    path.close()
+    torch.cuda.empty_cache()
+    uw, utw = gauge.prepare_links_window(u0, TS, HALO, wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
+    out["uw"], out["utw"] = uw[HALO - 1:HALO + 2], utw[HALO:HALO + 1]
+    return out
+
+
+def test_eigensolver_converged_every_slice(paper):
+    rep = paper["rep"]
+    assert rep.nconv == paper["wl"].nv and rep.max_resid <= 12 * 1e-13
+
+
+def test_eigenpairs_sampled_slice(paper):
+    nv = paper["wl"].nv
+    ev_o, vec_o = laplacian.lowest_eigpairs(paper["utw"], nv, "sparse")
+    ev_g = paper["evals"][TS]
+    assert np.abs(ev_g - ev_o[0]).max() <= 1e-10 * np.abs(ev_o).max()
+    assert laplacian.eigenprojector_distance(paper["evecs"][None], vec_o) <= 1e-8
+
+
+def test_noise_table_bit_exact(paper):
+    wl = paper["wl"]
+    assert np.array_equal(paper["codes"], onoise.z4_codes(wl.nt, wl.nv, 0, wl.config_id))
+
+
+def test_sources_project_to_diluted_noise(paper):
+    wl = paper["wl"]
+    rho = onoise.z4_values(onoise.z4_codes(wl.nt, wl.nv, 0, wl.config_id))[TS]      # [alpha][n]
+    V = paper["evecs"]                                                             # [n][V3][3]
+    for i, b in enumerate(paper["bs"]):
+        y = paper["rhs"][i].reshape(-1, 4, 3)
+        c = np.einsum("nxc,ab,xbc->an", V.conj(), GAMMA[3], y)
+        ref = dl.full_projector_diag(paper["spec"].dil, wl.nt, wl.nv, b)[TS] * rho
+        assert np.abs(c - ref).max() <= 1e-12, b
+
+
+def test_solves_true_residual_on_sampled_slice(paper):
+    wl = paper["wl"]
+    assert max(r.true_resid for r in paper["reps"]) <= 1e-10
+    piece = FastK(WilsonClover(np.ascontiguousarray(paper["uw"]), wl.m0, wl.csw, wl.xi))
+    for i in range(BLOCK):
+        row = piece.apply(np.ascontiguousarray(paper["sol"][i]))[1]
+        res = np.linalg.norm(paper["rhs"][i] - row) / paper["bnorm"][i]
+        assert res <= 1e-10, (i, res)
+
+
+def test_sinks_sampled_definition(paper):
+    V = paper["evecs"]
+    rng = np.random.default_rng(9)
+    for _ in range(16):
+        i, a, n = rng.integers(BLOCK), rng.integers(4), rng.integers(paper["wl"].nv)
+        x = paper["sol"][i, 1].reshape(-1, 4, 3)[:, a, :]
+        ref = np.sum(V[n].conj() * x)
+        assert abs(paper["coef"][i, a, n] - ref) <= 1e-12 * max(abs(ref), np.abs(paper["coef"][i]).max())
