@@ -125,9 +125,12 @@ int laph_stout_smear(laph_ctx *ctx, const laph_lattice *lat, void *links, double
  *            applied: its largest-modulus component (the first in storage
  *            order among those within a relative 1e-8 of the largest) is real
  *            and positive.
- *   params   NULL for defaults (lambda_L = 15, lambda_C chosen from a short
- *            Lanczos run, Chebyshev order 24, Krylov dimension
- *            max(2 nv + 16, nv + 32), tolerance 1e-11 on ||(-Delta) v - lambda v||
+ *   params   NULL for defaults (lambda_L = 15, lambda_C chosen per slice from a
+ *            short Lanczos run refined by one filtered cycle: 1.5 times the
+ *            largest Rayleigh quotient of the wanted Ritz vectors plus 0.02,
+ *            raised until the filter's gain over the wanted range is <= 1e3;
+ *            Chebyshev order 16, Krylov dimension
+ *            max(2 nv + 16, nv + 32), tolerance 1e-13 on ||(-Delta) v - lambda v||
  *            relative to ||-Delta|| <= 12, at most 50 restarts).
  *   report   optional (may be NULL).
  * Returns LAPH_ERR_NOT_CONVERGED (outputs still written) if some pair misses
@@ -136,10 +139,10 @@ int laph_stout_smear(laph_ctx *ctx, const laph_lattice *lat, void *links, double
 typedef struct {
     double lambda_L;      /* upper bound of the spectrum of -Delta (<= 0: 15)     */
     double lambda_C;      /* cutoff mapped to 1 (<= 0: automatic)                 */
-    int cheb_order;       /* n of T_n (<= 0: 24)                                  */
+    int cheb_order;       /* n of T_n (<= 0: 16)                                  */
     int krylov_dim;       /* Krylov space dimension m (<= 0: automatic)           */
     int max_restarts;     /* (<= 0: 50)                                           */
-    double tol;           /* residual tolerance relative to 12 (<= 0: 1e-11)      */
+    double tol;           /* residual tolerance relative to 12 (<= 0: 1e-13)      */
     uint64_t seed;        /* start vector seed (0: the all-equal start vector)    */
 } laph_eig_params;
 
@@ -366,16 +369,20 @@ int correlate(laph_ctx *ctx, const laph_lattice *lat, const laph_corr_spec *spec
  * processes whose device memory is reserved up front, or loops that must not
  * stall on an allocation).  It calls no cudaMalloc/cudaFree and no allocating
  * library routine and needs no laph_ctx.
- *   - coef[k], noise[k] and corr must be device pointers (LAPH_ERR_ARG
- *     otherwise: host arrays would need staging memory); spec->b_list is a
- *     host array.
+ *   - coef[k], noise[k] and corr must be device pointers of one device
+ *     (LAPH_ERR_ARG otherwise: host arrays would need staging memory); the
+ *     call runs on that device (made current for the call, the caller's
+ *     current device restored on return), and a stream other than the
+ *     default ones must belong to it.  spec->b_list is a host array of at
+ *     most 512 entries, passed to the device as a kernel argument.
  *   - Scratch comes from one fixed 16 MiB __device__ array inside the
  *     library, held by every GPU that loads it until the process exits.  A
- *     problem needing more (about 2 nt nb^2 + 3 nt nb^2 for pi pi complex
- *     doubles) is rejected with LAPH_ERR_ARG and a message giving the size.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress with that device current); make that first call
- *     before any stream capture.
+ *     problem needing more (about nt nb^2 complex doubles for a meson
+ *     channel, 5 nt nb^2 for pi pi) is rejected with LAPH_ERR_ARG and a
+ *     message giving the size.
+ *   - Each call looks up the array's device address (cudaGetSymbolAddress)
+ *     on its device; the first call on a device also loads the library's
+ *     kernels there, so make that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents: calls
  *     that overlap on the GPU (unordered streams or threads) race on it.
  * ------------------------------------------------------------------------ */

@@ -39,6 +39,22 @@ __global__ void normal_fill_kernel(long n, uint32_t seed, uint32_t stream, c64 *
     out[i] = c64{r * cs, r * sn};
 }
 
+// Column c of slice t of V ([t][keep][n]) is refilled with a seeded Gaussian vector where
+// mask[t * keep + c] is set (Philox counter (element, t keep + c, 1), key (seed, 0x5EED)).
+__global__ void randomize_cols_kernel(long n, int keep, const int *mask, uint32_t seed, c64 *V) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long col = (long)blockIdx.z * keep + blockIdx.y;
+    if (i >= n || !mask[col]) return;
+    uint32_t c[4] = {(uint32_t)i, (uint32_t)(i >> 32), (uint32_t)col, 1u};
+    philox4x32_10(c, seed, 0x5EEDu);
+    double u1 = ((double)c[0] + 0.5) * (1.0 / 4294967296.0);
+    double u2 = ((double)c[1] + 0.5) * (1.0 / 4294967296.0);
+    double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    V[col * n + i] = c64{r * cs, r * sn};
+}
+
 void philox_normal_fill(c64 *out, long n, uint32_t seed, uint32_t stream, cudaStream_t s) {
     normal_fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, seed, stream, out);
     LAPH_LAUNCH_CHECK();
@@ -589,7 +605,7 @@ extern "C" int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *
         laph_eig_params prm{};
         if (params) prm = *params;
         double lamL = prm.lambda_L > 0 ? prm.lambda_L : 15.0;
-        int ncheb = prm.cheb_order > 0 ? prm.cheb_order : 24;
+        int ncheb = prm.cheb_order > 0 ? prm.cheb_order : 16;
         int m = prm.krylov_dim > 0 ? prm.krylov_dim : std::max(2 * nv + 16, nv + 32);
         m = (int)std::min<long>(m, n - 1);
         LAPH_REQUIRE(m > nv, "krylov_dim must exceed nv");
@@ -675,22 +691,15 @@ extern "C" int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *
             int idx = std::min(nv + 8, mest - 1);
             for (int t = 0; t < nt; ++t) lamC[t] = std::min(-h_theta[(size_t)t * mest + idx], 0.8 * lamL);
         }
-        // 2) Chebyshev-accelerated thick-restart Lanczos
-        set_map(lamC, ncheb);
-        start_vector();
         int keep = std::min(m - 12, std::max(nv, nv + (m - nv) / 2));
         keep = std::max(keep, nv);
-        int j0 = 0, restarts = 0;
         std::vector<double> h_res((size_t)nt * nv), h_mu((size_t)nt * nv);
-        double worst = 0.0, prev_worst = 1e300;
-        int slow = 0, polish_iters = 0;
-        bool done = false;
-        for (restarts = 0; restarts <= max_restarts && !done; ++restarts) {
+        // One Lanczos cycle (steps j0 .. m-1) on the current map, its Ritz vectors Vt = V Y[:, :keep]
+        // and the Rayleigh quotients mu and residuals of the nv wanted ones on -Delta itself.
+        auto cycle = [&](int j0) {
             for (int j = j0; j < m; ++j) lz.step(j);
             run_jacobi(nt, m, m + 1, lz.H, J, Yraw, Y, theta, false, s);
-            // Ritz vectors Vt = V Y[:, :keep]
             rotate(n, nt, m + 1, m, keep, lz.V, Y, Vt, s);
-            // residuals of the wanted nv on -Delta itself
             {
                 std::vector<double> one(nt, 1.0), zero(nt, 0.0);
                 // LY = (-Delta) Y  with a = 1, b = 0 (temporarily swap the map coefficients)
@@ -709,6 +718,46 @@ extern "C" int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *
                 LAPH_CUDA(cudaMemcpyAsync(h_mu.data(), mu, sizeof(double) * nt * nv, cudaMemcpyDeviceToHost, s));
                 LAPH_CUDA(cudaStreamSynchronize(s));
             }
+        };
+        // 1b) refined cutoff: the short unaccelerated run bounds lambda_{nv+8} only loosely when the
+        //     low end of the spectrum is clustered (on a 24^3 slice it gave about 11 for wanted
+        //     eigenvalues near 0.2, which leaves the filter almost flat).  One Chebyshev-filtered
+        //     cycle of order 8 on that loose map already points the wanted Ritz vectors at the low
+        //     eigenvectors; the cutoff becomes 1.5 times the largest of their Rayleigh quotients on
+        //     -Delta (plus 0.02; the paper's 24^3 runs took lambda_C = 0.5 for N_v = 112, about 1.5
+        //     lambda_{N_v} there), never above the loose estimate.
+        if (!(prm.lambda_C > 0)) {
+            set_map(lamC, std::min(ncheb, 8));
+            start_vector();
+            cycle(0);
+            // The cutoff is raised where needed so that the filter amplifies no wanted eigenvalue
+            // more than 1e3 times as much as the largest wanted one (T_n(B(0)) / T_n(B(mu_max)), -Delta
+            // >= 0): a wider range puts the FP64 rounding floor of the filtered vectors, about
+            // eps times that ratio, near the tolerance (seen on 4^3 slices, where N_v = 8 ends
+            // inside the shell near 2).
+            auto log_t = [&](double x) { return ncheb * std::acosh(std::max(x, 1.0)); };   // ~ log T_n(x), x >= 1
+            for (int t = 0; t < nt; ++t) {
+                double mx = 0.0;
+                for (int i = 0; i < nv; ++i) mx = std::max(mx, h_mu[(size_t)t * nv + i]);
+                if (!(std::isfinite(mx) && mx > 0.0)) continue;
+                double c = 1.5 * mx + 0.02;
+                for (int k = 0; k < 200 && c < lamC[t]; ++k) {
+                    const double b0 = 1.0 + 2.0 * c / (lamL - c), bm = 1.0 + 2.0 * (c - mx) / (lamL - c);
+                    if (log_t(b0) - log_t(bm) <= std::log(1e3)) break;
+                    c *= 1.05;
+                }
+                lamC[t] = std::min(lamC[t], c);
+            }
+        }
+        // 2) Chebyshev-accelerated thick-restart Lanczos
+        set_map(lamC, ncheb);
+        start_vector();
+        int j0 = 0, restarts = 0;
+        double worst = 0.0, prev_worst = 1e300;
+        int slow = 0, polish_iters = 0;
+        bool done = false;
+        for (restarts = 0; restarts <= max_restarts && !done; ++restarts) {
+            cycle(j0);
             worst = 0.0;
             for (double r : h_res) worst = std::max(worst, std::isfinite(r) ? r : 1e300);
             if (worst <= tol * 12.0) {
@@ -721,7 +770,7 @@ extern "C" int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *
             // pass from there) or stop gaining (twice less than a factor 2).
             slow = (worst > 0.5 * prev_worst) ? slow + 1 : 0;
             prev_worst = std::min(prev_worst, worst);
-            if (restarts == max_restarts || worst < 1e-8 || (slow >= 2 && worst < 1e-4)) break;
+            if (restarts == max_restarts || worst < 1e-8 || (slow >= 2 && worst < 1e-4) || slow >= 4) break;
             // thick restart: V[:, :keep] = Vt, V[:, keep] = V[:, m]; H = diag(theta) + coupling row
             copy_slices_kernel<<<dim3(grid_for(n, 256), nt), 256, 0, s>>>(n, lz.V + (long)m * n, (long)(m + 1) * n,
                                                                           lz.w, n);
@@ -771,6 +820,22 @@ extern "C" int laph_eigvecs(laph_ctx *ctx, const laph_lattice *lat, const void *
             std::vector<double> one(nt, 1.0), zero(nt, 0.0);
             // passes continue while they gain: at most 100, and never after three passes in a row
             // that each cut the worst residual by less than 10 %
+            // A single start vector puts only one direction of each exactly degenerate eigenspace
+            // into the Krylov space (the free field: every level at least three-fold).  Before the
+            // block iteration, every kept column that is not a wanted Ritz vector with residual
+            // <= 1e-8 is replaced by a seeded random vector, so the block spans the missing
+            // partners; the filter turns the random columns into low modes within a pass or two.
+            {
+                std::vector<int> hm((size_t)nt * keep, 1);
+                for (int t = 0; t < nt; ++t)
+                    for (int i = 0; i < nv; ++i) hm[(size_t)t * keep + i] = !(h_res[(size_t)t * nv + i] <= 1e-8);
+                int *dm = (int *)ws_get(ctx, "eig:rmask", sizeof(int) * nt * (size_t)keep);
+                LAPH_CUDA(cudaMemcpyAsync(dm, hm.data(), sizeof(int) * hm.size(), cudaMemcpyHostToDevice, s));
+                randomize_cols_kernel<<<dim3(grid_for(n, 256), keep, nt), 256, 0, s>>>(n, keep, dm,
+                                                                                      (uint32_t)(seed ^ 0xA5A5u), Vt);
+                LAPH_LAUNCH_CHECK();
+                LAPH_CUDA(cudaStreamSynchronize(s));
+            }
             double pol_prev = worst;
             int pol_flat = 0;
             for (int it = 0; it < 100 && !done && pol_flat < 3; ++it, ++polish_iters) {
