@@ -1,23 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the stochastic-LapH quark-line path on GB300.
 
-One step = one pass of the whole hot path over one batch of synthetic input:
-Laplacian eigenvectors of every slice (a1), Z4 diluted sources for two noises
-(a2), the batched solves of all diluted sources to FP64 true residual 1e-10
-(a3), sink coefficients (a4) and the pion / scalar / rho correlators (a5).
-Gauge preparation (stout smearing, a0) is setup and not timed.  Steps are
-pipelined: a second library context computes the next batch's eigenvectors on
-its own stream while this batch's sources, solves, sinks and correlators run
-(--no-overlap runs the stages of each step one after another).
+Default workload: the paper-shaped lattice 24^3 x 128, xi = 3.5, N_v = 64, dilution
+(TI16, SF, LI8): 16 time-interlace groups x 4 spins x 8 LapH projectors = 512 diluted
+sources per noise, four noises (two pion lines and the four lines of the I = 2 pi pi
+correlator).  Per gauge configuration the Laplacian eigenvectors of all 128 slices are
+computed once (a1, reported separately, as are gauge smearing and the sources).  One step =
+one block of B diluted sources of one noise (default B = 32: one time-interlace group):
+Z4 sources (a2), one batched mixed-precision solve of the block to FP64 true residual 1e-10
+(a3), sink coefficients (a4); after the last noise of a group, the pion and I = 2 pi pi
+correlators of that group's eight source times (a5).  Steps cycle through noises and groups.
 
-Default workload: 16^3 x 32, xi = 3.5, N_v = 32, (TF, SF, LI8) at four source
-times (0, 8, 16, 24), two noises -> 256 diluted sources per step (seeded synthetic
-gauge field).
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--block B]
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-
-Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
-replica (its own noises); value = sources of all ranks / max rank time.
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent replica (its
+own noises); value = sources of all ranks / max rank time.  `--workload medium_16x32` runs
+the 16^3 x 32 pipelined whole-path step instead (eigenvectors in every step).
 
     python bench.py --dslash-sweep [--dslash-nr 1,8,16,32,64] [--dslash-iters 50]
 
@@ -48,9 +46,13 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="medium_16x32")
+    p.add_argument("--workload", default="paper_24x128")
     p.add_argument("--mode", choices=["mixed", "plain"], default="mixed")
-    p.add_argument("--plain-sample", type=int, default=2, help="sources solved by the plain FP64 comparison")
+    p.add_argument("--block", type=int, default=32, help="diluted sources per step (paper-shaped workload; 8, 16 "
+                                                           "or 32: a time-interlace group is 32)")
+    p.add_argument("--variants", action="store_true",
+                   help="also time the single-change ablations (paper-shaped workload; minutes)")
+    p.add_argument("--plain-sample", type=int, default=1, help="sources solved by the plain FP64 comparison")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per solver launch (0: autotuned)")
     p.add_argument("--no-overlap", action="store_true",
@@ -158,38 +160,48 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
-def oracle_sample(wl, seconds=15.0, threads=None):
-    """Times the oracle's plain-C BiCGStab (oracle/c/oracle_dirac.c, one solve per
-    thread) for a bounded number of iterations and scales to sources/s with the
-    iteration count a full solve needs at this m0 (oracle/m0_tuned.json)."""
+def oracle_sample(wl, seconds=15.0, threads=None, _cache={}):
+    """Times the oracle's plain-C BiCGStab (oracle/c/oracle_dirac.c, one single-thread solve per
+    host core, run concurrently) for a bounded number of iterations and scales to sources/s
+    with the iteration count a full solve to 1e-10 takes at this m0 (oracle/m0_tuned.json).
+    The loops' work does not depend on the link or clover values, so the seeded unsmeared links
+    are used and, on lattices too large for the numpy clover (more than 2e5 sites), the site
+    matrix without its clover term (the C loops still multiply by the full 12x12 matrix)."""
     from oracle.dirac import WilsonClover
     from oracle.fast import FastK
     import synth
     cores = threads or os.cpu_count() or 1
-    # iteration timing does not depend on the link values; unsmeared seeded links suffice
-    u0 = wl.gauge()
-    fk = FastK(WilsonClover(u0, wl.m0, wl.csw, wl.xi))
-    b = synth.random_spinor(wl.ns, wl.nt, seed=7, nrhs=cores)
-    t = time.perf_counter()
-    fk.solve(b[:1], tol=1e-30, maxiter=4, nthreads=1)
-    per_iter = (time.perf_counter() - t) / 4.0
+    big = wl.volume > 200_000
+    key = (wl.name, cores)
+    if key not in _cache:
+        fk = FastK(WilsonClover(wl.gauge(), wl.m0, 0.0 if big else wl.csw, wl.xi))
+        one = synth.random_spinor(wl.ns, wl.nt, seed=7)
+        _cache[key] = (fk, np.ascontiguousarray(np.broadcast_to(one, (cores,) + one.shape)))
+    fk, b = _cache[key]
     tuned = os.path.join(ROOT, "oracle", "m0_tuned.json")
     need = wl.target_iters
     if os.path.exists(tuned):
         rec = json.load(open(tuned)).get(wl.name)
         if rec:
             need = rec["iters"]
-    # stay below the length of a full solve so every thread runs exactly `iters` iterations
-    iters = max(4, min(int(seconds / max(per_iter, 1e-6)), need // 2))
+    if big:
+        iters = 1 if seconds < 10 else 2
+    else:
+        t = time.perf_counter()
+        fk.solve(b[:1], tol=1e-30, maxiter=4, nthreads=1)
+        per_iter = (time.perf_counter() - t) / 4.0
+        # stay below the length of a full solve so every thread runs exactly `iters` iterations
+        iters = max(4, min(int(seconds / max(per_iter, 1e-6)), need // 2))
     t = time.perf_counter()
     _, its, _ = fk.solve(b, tol=1e-30, maxiter=iters, nthreads=cores)
     wall = time.perf_counter() - t
     iters = int(np.mean(its))
     rate = cores / (wall * need / iters)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{cores} concurrent single-thread oracle BiCGStab solves (plain C, full operator) run for "
-                      f"{iters} iterations in {wall:.1f} s, scaled to the {need} iterations a solve to 1e-10 takes "
-                      f"at this m0; eigenvectors, sources, sinks and contractions not included"}
+            "sample": f"{cores} concurrent single-thread oracle BiCGStab solves (plain C, full operator"
+                      f"{', site term without clover' if big else ''}) on {wl.ns}^3x{wl.nt} run for {iters} "
+                      f"iterations in {wall:.1f} s, scaled to the {need} iterations a solve to 1e-10 takes at "
+                      f"this m0; eigenvectors, sources, sinks and contractions not included"}
 
 
 # ----------------------------------------------------------------------------- ncu traffic record
@@ -392,8 +404,267 @@ def profiled_step(L, torch, st, u, ut):
     return {"stage_ms": stages, "family_ms": fams}
 
 
-# ----------------------------------------------------------------------------- our arm
+class StreamStep:
+    """One step of the paper-shaped workload: B diluted sources of one noise (a2), their batched
+    mixed solve (a3) and sink coefficients (a4); after the last block of the last noise of a
+    time-interlace group, the correlators of the group's source times (a5).  Step i works on
+    noise (i // parts) % nnoise and group (i // (parts nnoise)) % nT, part i % parts of its 32
+    projectors, so consecutive steps cycle through every source of a configuration."""
+
+    def __init__(self, L, torch, path, spec, wl, rank, mode, block, evecs):
+        from paper_1104_3870_gb300.pipeline import n_projectors
+        self.L, self.torch, self.path, self.wl, self.mode = L, torch, path, wl, mode
+        (kT, JT), (kS, JS), (kL, JL) = spec.dil
+        assert kT == 3, "the streaming step expects time interlacing"
+        self.nT = JT
+        nS, nL = n_projectors(kS, JS, 4), n_projectors(kL, JL, wl.nv)
+        self.groups = [[(g * nS + a) * nL + l for a in range(nS) for l in range(nL)] for g in range(self.nT)]
+        self.ng = len(self.groups[0])
+        assert self.ng % block == 0, "the block must divide a time-interlace group"
+        self.block, self.parts = block, self.ng // block
+        self.nnoise = wl.n_noise
+        self.noise_ids = replica_noise_ids(rank, self.nnoise)
+        self.evecs = evecs
+        self.rhs = path.field(block)
+        self.sol = torch.empty_like(self.rhs)
+        dev = self.rhs.device
+        self.coef = torch.empty((self.nnoise, self.ng, wl.nt, 4, wl.nv), dtype=torch.complex128, device=dev)
+        self.codes = torch.empty((self.nnoise, wl.nt, 4, wl.nv), dtype=torch.uint8, device=dev)
+        self.ntimes = wl.nt // self.nT
+        self.corr = torch.zeros((3, self.ntimes, wl.nt), dtype=torch.complex128, device=dev)
+        self.coef_host = torch.empty((block, wl.nt, 4, wl.nv), dtype=torch.complex128).pin_memory()
+        self.i = 0
+        self.stats = {"iters_max": 0, "resid_max": 0.0, "correlator_groups": 0}
+
+    def where(self, i):
+        part = i % self.parts
+        k = (i // self.parts) % self.nnoise
+        g = (i // (self.parts * self.nnoise)) % self.nT
+        return k, g, part
+
+    def run(self, u_in, read_back=False, events=None):
+        p, L = self.path, self.L
+        mark = (lambda j: events[j].record(self.torch.cuda.current_stream())) if events else (lambda j: None)
+        k, g, part = self.where(self.i)
+        lo = part * self.block
+        bs = self.groups[g][lo:lo + self.block]
+        mark(0)
+        p.sources(self.evecs, self.noise_ids[k], self.wl.config_id, bs, out=self.rhs, codes=self.codes[k])
+        mark(1)
+        _, reps = p.solve(u_in, self.rhs, mode=self.mode, sol=self.sol, rhs_block=self.block)
+        mark(2)
+        p.sinks(self.evecs, self.sol, out=self.coef[k, lo:lo + self.block])
+        mark(3)
+        if k == self.nnoise - 1 and part == self.parts - 1:
+            bg = self.groups[g]
+            c, n = self.coef, self.codes
+            for j in range(self.ntimes):
+                t0 = g + j * self.nT
+                p.correlate(L.CH_PION, t0, bg, [c[0], c[1]], [n[0], n[1]], out=self.corr[0, j])
+                if self.nnoise >= 4:
+                    p.correlate(L.CH_PION, t0, bg, [c[2], c[3]], [n[2], n[3]], out=self.corr[1, j])
+                    p.correlate(L.CH_PIPI_I2, t0, bg, [c[0], c[1], c[2], c[3]], [n[0], n[1], n[2], n[3]],
+                                out=self.corr[2, j])
+            self.stats["correlator_groups"] += 1
+        mark(4)
+        if read_back:
+            self.coef_host.copy_(self.coef[k, lo:lo + self.block], non_blocking=True)
+        self.stats["iters_max"] = max(self.stats["iters_max"], max(r.iters for r in reps))
+        self.stats["resid_max"] = max(self.stats["resid_max"], max(r.true_resid for r in reps))
+        self.i += 1
+
+
+def roofline_from(L, fam_name, kernel, n, kms, kbytes, hbm_peak, peaks, ratio):
+    achieved = kbytes / (kms / 1000.0) / 1e9 if kms else None
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": (achieved / hbm_peak) if achieved else None,
+            "traffic": ratio * kbytes / n if (ratio and n) else None,
+            "kernel": kernel, "family": fam_name, "launches": n, "avg_launch_us": 1000.0 * kms / n if n else None,
+            "algorithmic_bytes_per_launch": kbytes / n if n else None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+
+
+def run_stream(args):
+    """The paper-shaped workload (see the module docstring): eigenvectors once, then K timed
+    steps of B diluted sources each."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1104_3870_gb300 import build
+    build.build()
+    from paper_1104_3870_gb300 import laph as L
+    from paper_1104_3870_gb300.pipeline import LapHPath, LatticeSpec
+    import synth
+
+    wl = synth.WORKLOADS[args.workload]
+    spec = LatticeSpec(wl.ns, wl.nt, wl.xi, wl.m0, wl.csw, wl.nv, (wl.dil_time, wl.dil_spin, wl.dil_laph),
+                       wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
+    path = LapHPath(spec, local)
+    stream = torch.cuda.current_stream()
+
+    def ev_pair():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    setup = {}
+    t = time.perf_counter()
+    u0 = wl.gauge()
+    setup["gauge_host_s"] = time.perf_counter() - t
+    a, b = ev_pair()
+    a.record(stream)
+    u, ut = path.prepare_links(u0)                       # a0: setup
+    b.record(stream)
+    del u0
+    e0, e1 = ev_pair()
+    e0.record(stream)
+    evals, evecs, erep = path.eigvecs(ut)                # a1: once per configuration
+    e1.record(stream)
+    torch.cuda.synchronize()
+    setup["smear_ms"] = a.elapsed_time(b)
+    setup["eigvecs_ms"] = e0.elapsed_time(e1)
+    setup["eigvecs"] = {"restarts": erep.restarts, "matvecs_per_slice": erep.matvecs, "nconv": erep.nconv,
+                        "max_resid": erep.max_resid, "lambda_C_max": erep.lambda_C}
+    del ut
+    mode = L.MIXED_FP32 if args.mode == "mixed" else L.PLAIN_FP64
+    st = StreamStep(L, torch, path, spec, wl, rank, mode, args.block, evecs)
+
+    for _ in range(args.warmup):
+        st.run(u)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local) if rank == 0 else None
+    L.laph_profile_enable(0)
+    launches0 = L.laph_launch_count()
+    t0, t1 = ev_pair()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        st.run(u)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = L.laph_launch_count() - launches0
+    clk = clocks.stop() if clocks else None
+    ms = t0.elapsed_time(t1) / args.steps
+    ms_max = aggregate_max(ms, world, device="cuda")
+    barrier(world)
+    value = whole_job_rate(args.block, world, ms_max / 1000.0)
+
+    # roofline of the dominant kernel family from a separate pass with per-launch event timing
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    L.laph_profile_reset()
+    L.laph_profile_enable(1)
+    for _ in range(2):
+        st.run(u)
+    torch.cuda.synchronize()
+    L.laph_profile_enable(0)
+    fam = "dslash_fp32" if mode == L.MIXED_FP32 else "dslash_fp64"
+    n, kms, kbytes, _ = L.laph_profile_read(fam)
+    ratio = measured_traffic_ratio(wl.name)
+    kernel = "FP32 even-odd hop (hop3_kernel, TMA-fed)" if mode == L.MIXED_FP32 else "hop_kernel<double>"
+    roofline = roofline_from(L, fam, kernel, n, kms, kbytes, hbm_peak, peaks, ratio)
+    roofline["note"] = "two untimed steps with every stencil launch timed by CUDA events on its stream"
+
+    # breakdown: one more step with every kernel family timed, and per-stage events
+    L.laph_profile_reset()
+    L.laph_profile_enable(2)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    st.run(u, events=evs)
+    torch.cuda.synchronize()
+    L.laph_profile_enable(0)
+    stages = {nm: evs[j].elapsed_time(evs[j + 1]) for j, nm in enumerate(["sources", "solve", "sinks", "correlate"])}
+    fams = {}
+    for f in L.laph_profile_families():
+        nn, fms, fby, _ = L.laph_profile_read(f)
+        fams[f] = {"launches": nn, "ms": fms, "bytes": fby,
+                   "GBs": (fby / (fms / 1000.0) / 1e9) if (fms and fby) else None}
+    L.laph_profile_reset()
+
+    # e2e through the public API with host buffers: the links sit in pinned host memory and are
+    # staged by the library in every solve; the step's coefficients are read back to the host.
+    u_h = u.cpu().pin_memory()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        st.run(u_h, read_back=True)
+    torch.cuda.synchronize()
+    e2e_s = aggregate_max((time.perf_counter() - t) / max(args.e2e_steps, 1), world, device="cuda")
+    e2e = {"value": whole_job_rate(args.block, world, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": int(u_h.numel() * u_h.element_size()),
+           "d2h_bytes_per_step": int(st.coef_host.numel() * st.coef_host.element_size())}
+    del u_h
+
+    variants = stream_variants(L, torch, path, wl, u, st, args, mode)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64" if mode == L.MIXED_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": f"{wl.name}: {wl.ns}^3x{wl.nt}, xi={wl.xi}, N_v={wl.nv}, dilution (TI{st.nT}, SF, "
+                                   f"LI8), {st.ng * st.nT} diluted sources per noise, {st.nnoise} noises per "
+                                   f"replica, m0={wl.m0}",
+                       "sources_per_step": args.block, "solver": args.mode, "tol": 1e-10, "rhs_block": args.block,
+                       "step": "Z4 sources + one batched solve + sinks of one block (+ the correlators of a "
+                               "time-interlace group after its last block); eigenvectors once per configuration "
+                               "(setup.eigvecs_ms)",
+                       "l2": "inputs larger than L2 (one block's solver fields > 10 GB)",
+                       "parallelism": f"replicas{world}"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "setup": setup, "breakdown": {"stage_ms": stages, "family_ms": fams}, "variants": variants,
+            "path_stats": dict(st.stats)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(wl)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    path.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def stream_variants(L, torch, path, wl, u, st, args, mode):
+    """Comparisons on samples of the workload's own diluted sources, each timed with CUDA events
+    on the current stream: the plain FP64 solve one right-hand side per launch (the baseline the
+    reshaped solver must beat) and, with --variants, the single-change ablations."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    if mode != L.MIXED_FP32 or args.plain_sample <= 0:
+        return out
+
+    def timed_solve(n, prm):
+        sub = st.rhs[:n].clone()
+        xs = torch.empty_like(sub)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        reps = L.dirac_solve_batch(path.ctx, path.lat, u, wl.m0, wl.csw, sub, xs, n, prm)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return {"sources_per_s": n / (a0.elapsed_time(a1) / 1000.0), "sample": n,
+                "iters": [r.iters for r in reps], "true_resid_max": max(r.true_resid for r in reps)}
+
+    n = min(args.plain_sample, args.block)
+    out["plain_fp64_one_rhs"] = timed_solve(n, L.solver_params(mode=L.PLAIN_FP64, rhs_block=1))
+    if args.variants:
+        out["ablations"] = {
+            "precision_only: mixed FP32/FP64, one RHS per launch":
+                timed_solve(min(2, args.block), L.solver_params(mode=L.MIXED_FP32, rhs_block=1)),
+            "batching_only: plain FP64, 8 RHS per launch":
+                timed_solve(min(8, args.block), L.solver_params(mode=L.PLAIN_FP64, rhs_block=8)),
+        }
+    return out
+
+
 def run_ours(args):
+    if args.workload == "paper_24x128":
+        run_stream(args)
+    else:
+        run_path(args)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_path(args):
     import torch
     rank, world, local = dist_env()
     if world > 1:

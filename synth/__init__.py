@@ -126,10 +126,11 @@ WORKLOADS = {
                              gauge_seed=1001, dil_time=(DIL_FULL, 0), dil_spin=(DIL_FULL, 0),
                              dil_laph=(DIL_INTERLACE, 8), source_times=(0, 8, 16, 24), n_noise=2,
                              target_iters=600),
-    # 24^3x128, N_v = 64, (TI16, SF, LI8): 512 diluted sources per noise.  m0 from the seeded
-    # bisection of the plain FP64 iteration count (1351 iterations to 1e-10, target 1500).
+    # 24^3x128, N_v = 64, (TI16, SF, LI8): 512 diluted sources per noise, four noises (two pion
+    # lines and the four lines of the I = 2 pi pi correlator).  m0 from the seeded bisection of the
+    # plain FP64 iteration count (1351 iterations to 1e-10, target 1500).
     "paper_24x128": Workload("paper_24x128", ns=24, nt=128, xi=3.5, csw=1.0, m0=-0.0003125, nv=64,
                              gauge_seed=1002, dil_time=(DIL_INTERLACE, 16), dil_spin=(DIL_FULL, 0),
-                             dil_laph=(DIL_INTERLACE, 8), source_times=(0,), n_noise=2,
+                             dil_laph=(DIL_INTERLACE, 8), source_times=(0,), n_noise=4,
                              target_iters=1500),
 }
