@@ -47,7 +47,8 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="paper_24x128")
-    p.add_argument("--mode", choices=["mixed", "plain"], default="mixed")
+    p.add_argument("--mode", choices=["mixed", "bf16", "plain"], default="mixed",
+                   help="mixed: FP32 inner solver; bf16: BF16-stored inner solver; plain: FP64 BiCGStab")
     p.add_argument("--block", type=int, default=32, help="diluted sources per step (paper-shaped workload; 8, 16 "
                                                            "or 32: a time-interlace group is 32)")
     p.add_argument("--variants", action="store_true",
@@ -205,17 +206,18 @@ def oracle_sample(wl, seconds=15.0, threads=None, _cache={}):
 
 
 # ----------------------------------------------------------------------------- ncu traffic record
-HOP_KERNEL_VERSION = "hop3_tma_ns2_rpt2"
+HOP_KERNEL_VERSION = "hop3_tma_ns2_zblock8"
 
 
-def measured_traffic_ratio(workload):
-    """DRAM bytes over algorithmic bytes of one captured FP32 hop launch (hop3_kernel), from the
-    committed ncu summary (profiles/hop3_kernel_fp32_<workload>.md, line
-    'traffic_bytes_per_launch: N version V nr R algorithmic A'); None when absent or taken on
-    another kernel version.  The capture uses a smaller RHS block than the bench (device
-    memory rule for ncu); traffic scales with the sites x RHS processed, so the bench
+def measured_traffic_ratio(workload, family="dslash_fp32"):
+    """DRAM bytes over algorithmic bytes of one captured hop launch (hop3_kernel) from the
+    committed ncu summary profiles/hop3_kernel_<precision>_<workload>.md, line
+    'traffic_bytes_per_launch: N version V nr R algorithmic A'; None when absent or taken on
+    another kernel version.  The capture runs a smaller lattice than the bench (the device
+    memory rule for ncu captures); traffic scales with the sites x RHS processed, so the bench
     reports ratio x its own algorithmic bytes per launch."""
-    path = os.path.join(ROOT, "profiles", f"hop3_kernel_fp32_{workload}.md")
+    prec = family.split("_")[-1]
+    path = os.path.join(ROOT, "profiles", f"hop3_kernel_{prec}_{workload}.md")
     if not os.path.exists(path):
         return None
     for line in open(path):
@@ -527,7 +529,7 @@ def run_stream(args):
     setup["eigvecs"] = {"restarts": erep.restarts, "matvecs_per_slice": erep.matvecs, "nconv": erep.nconv,
                         "max_resid": erep.max_resid, "lambda_C_max": erep.lambda_C}
     del ut
-    mode = L.MIXED_FP32 if args.mode == "mixed" else L.PLAIN_FP64
+    mode = {"mixed": L.MIXED_FP32, "bf16": L.MIXED_BF16, "plain": L.PLAIN_FP64}[args.mode]
     st = StreamStep(L, torch, path, spec, wl, rank, mode, args.block, evecs)
 
     for _ in range(args.warmup):
@@ -561,10 +563,12 @@ def run_stream(args):
         st.run(u)
     torch.cuda.synchronize()
     L.laph_profile_enable(0)
-    fam = "dslash_fp32" if mode == L.MIXED_FP32 else "dslash_fp64"
+    fam = {L.MIXED_FP32: "dslash_fp32", L.MIXED_BF16: "dslash_bf16"}.get(mode, "dslash_fp64")
     n, kms, kbytes, _ = L.laph_profile_read(fam)
-    ratio = measured_traffic_ratio(wl.name)
-    kernel = "FP32 even-odd hop (hop3_kernel, TMA-fed)" if mode == L.MIXED_FP32 else "hop_kernel<double>"
+    ratio = measured_traffic_ratio(wl.name, fam)
+    kernel = {"dslash_fp32": "FP32 even-odd hop (hop3_kernel, TMA-fed, FP32 spinors)",
+              "dslash_bf16": "even-odd hop (hop3_kernel, TMA-fed, BF16 spinors, FP32 links/clover/arithmetic)",
+              "dslash_fp64": "hop_kernel<double>"}[fam]
     roofline = roofline_from(L, fam, kernel, n, kms, kbytes, hbm_peak, peaks, ratio)
     roofline["note"] = "two untimed steps with every stencil launch timed by CUDA events on its stream"
 
@@ -600,7 +604,8 @@ def run_stream(args):
     variants = stream_variants(L, torch, path, wl, u, st, args, mode)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32/f64" if mode == L.MIXED_FP32 else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {L.MIXED_FP32: "f32/f64", L.MIXED_BF16: "bf16-storage/f32/f64"}.get(mode, "f64"),
+            "data": "synthetic",
             "config": {"workload": f"{wl.name}: {wl.ns}^3x{wl.nt}, xi={wl.xi}, N_v={wl.nv}, dilution (TI{st.nT}, SF, "
                                    f"LI8), {st.ng * st.nT} diluted sources per noise, {st.nnoise} noises per "
                                    f"replica, m0={wl.m0}",
@@ -629,7 +634,7 @@ def stream_variants(L, torch, path, wl, u, st, args, mode):
     reshaped solver must beat) and, with --variants, the single-change ablations."""
     stream = torch.cuda.current_stream()
     out = {}
-    if mode != L.MIXED_FP32 or args.plain_sample <= 0:
+    if mode == L.PLAIN_FP64 or args.plain_sample <= 0:
         return out
 
     def timed_solve(n, prm):

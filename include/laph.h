@@ -202,8 +202,11 @@ int laph_make_sources(laph_ctx *ctx, const laph_lattice *lat, const void *evecs,
  *                          (rhs_block = 1 is the one-at-a-time baseline).
  *   LAPH_SOLVE_MIXED_FP32  FP64 defect correction around FP32 even-odd
  *                          BiCGStab, all RHS of a block in one launch.
- *   LAPH_SOLVE_MIXED_BF16  reserved for BF16 storage of the inner stencil
- *                          operands; not available in this version (LAPH_ERR_ARG).
+ *   LAPH_SOLVE_MIXED_BF16  the same defect correction around an inner BiCGStab whose
+ *                          spinors and Krylov vectors are stored in BF16 (FP32
+ *                          arithmetic, FP32 links, clover and iterate; default
+ *                          inner_tol 1e-2); blocks of 32, 64, 128 or 256 RHS, a
+ *                          block of another size runs the FP32 inner solver.
  *   LAPH_SOLVE_LEARNED     FP64 defect correction around FP32 flexible GCR
  *                          with the learned right preconditioner `weights`
  *                          (layout of laph_precond_train).
@@ -310,12 +313,14 @@ int laph_dirac_apply(laph_ctx *ctx, const laph_lattice *lat, const void *links,
  * site index) / 2 runs over the Vh = V/2 sites of the field's parity and the right-hand
  * side index is innermost.  precision LAPH_PREC_FP64: c128 fields, the FP64 kernel;
  * LAPH_PREC_FP32: c64 fields, the packed-FP32 kernel of the mixed solver (links and
- * clover rounded to FP32).  `z` may be NULL for LAPH_HOP_CLOVINV.  Host or device
+ * clover rounded to FP32); LAPH_PREC_BF16: fields of bfloat16 pairs (re, im), the same kernel
+ * reading and writing BF16 spinors with FP32 links, clover and arithmetic (the inner operator of
+ * LAPH_SOLVE_MIXED_BF16; nrhs 32, 64, 128 or 256).  `z` may be NULL for LAPH_HOP_CLOVINV.  Host or device
  * pointers; links [V][4][3][3] c128.  Returns after the stream has drained, so that a
  * copy wait that gave up is reported (LAPH_ERR_TIMEOUT).  Errors: LAPH_ERR_ARG for a bad parity, mode or
  * precision, nrhs < 1 or a missing pointer. */
 enum { LAPH_HOP_CLOVINV = 0, LAPH_HOP_CLOVINV_XPAY = 1, LAPH_HOP_APPLY = 2 };
-enum { LAPH_PREC_FP64 = 0, LAPH_PREC_FP32 = 1 };
+enum { LAPH_PREC_FP64 = 0, LAPH_PREC_FP32 = 1, LAPH_PREC_BF16 = 2 };
 int laph_dslash_eo(laph_ctx *ctx, const laph_lattice *lat, const void *links, const laph_dirac_params *dirac,
                    int parity, int mode, int precision, const void *in, const void *z, void *out, int nrhs,
                    void *stream);

@@ -67,16 +67,17 @@ __global__ void red_final(const c64 *partial, int nblk, int nred, int nr, c64 *o
 }
 
 template <int NRED, class Body>
-static void run_reduce(laph_ctx *ctx, const RedPlan &pl, long nrows, const Body &body, c64 *out, cudaStream_t s) {
+static void run_reduce(laph_ctx *ctx, const RedPlan &pl, long nrows, const Body &body, c64 *out, cudaStream_t s,
+                       const char *family = nullptr, double bytes = 0.0) {
     c64 *partial = (c64 *)ws_get(ctx, "red:partial", sizeof(c64) * pl.grid * NRED * pl.nr);
     size_t shm = sizeof(c64) * NRED * pl.block;
-    const char *fam = sizeof(typename Body::Acc) == 8 ? "blas_fp32" : "blas_fp64";
+    const char *fam = family ? family : sizeof(typename Body::Acc) == 8 ? "blas_fp32" : "blas_fp64";
     prof_begin(fam, s);
     red_kernel<NRED, Body><<<pl.grid, pl.block, shm, s>>>(nrows, pl.nr, pl.rpb, body, partial);
     LAPH_LAUNCH_CHECK();
     red_final<<<NRED * pl.nr, 256, 0, s>>>(partial, (int)pl.grid, NRED, pl.nr, out);
     LAPH_LAUNCH_CHECK();
-    prof_end(fam, s, 0.0, 0.0);
+    prof_end(fam, s, bytes, 0.0);
 }
 
 void red_final_sum(const c64 *partial, int nblk, int nred, int nr, c64 *out, cudaStream_t s) {
@@ -125,12 +126,13 @@ struct Dots3 {
 template <typename T>
 void mrhs_dots(laph_ctx *ctx, const RedPlan &pl, long nrows, int nred, const cpx<T> *a0, const cpx<T> *b0,
                const cpx<T> *a1, const cpx<T> *b1, const cpx<T> *a2, const cpx<T> *b2, c64 *out, cudaStream_t s) {
+    const double by = 2.0 * nred * (double)nrows * pl.nr * sizeof(cpx<T>);   // two streams per product
     if (nred == 1)
-        run_reduce<1>(ctx, pl, nrows, Dots1<T>{a0, b0}, out, s);
+        run_reduce<1>(ctx, pl, nrows, Dots1<T>{a0, b0}, out, s, nullptr, by);
     else if (nred == 2)
-        run_reduce<2>(ctx, pl, nrows, Dots2<T>{a0, b0, a1, b1}, out, s);
+        run_reduce<2>(ctx, pl, nrows, Dots2<T>{a0, b0, a1, b1}, out, s, nullptr, by);
     else
-        run_reduce<3>(ctx, pl, nrows, Dots3<T>{a0, b0, a1, b1, a2, b2}, out, s);
+        run_reduce<3>(ctx, pl, nrows, Dots3<T>{a0, b0, a1, b1, a2, b2}, out, s, nullptr, by);
 }
 template void mrhs_dots<float>(laph_ctx *, const RedPlan &, long, int, const c32 *, const c32 *, const c32 *,
                                const c32 *, const c32 *, const c32 *, c64 *, cudaStream_t);
@@ -206,7 +208,7 @@ void bicg_p_update(long nrows, int nr, const BicgScalars &sc, const cpx<T> *r, c
     prof_begin(fam, s);
     p_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(n, nr, sc, r, p, v);
     LAPH_LAUNCH_CHECK();
-    prof_end(fam, s, 0.0, 0.0);
+    prof_end(fam, s, 4.0 * n * sizeof(cpx<T>), 0.0);   // read r, p, v; write p
 }
 
 template <typename T>
@@ -224,7 +226,7 @@ void bicg_s_update(long nrows, int nr, const BicgScalars &sc, const cpx<T> *r, c
     prof_begin(fam, s);
     s_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(n, nr, sc, r, v, sv);
     LAPH_LAUNCH_CHECK();
-    prof_end(fam, s, 0.0, 0.0);
+    prof_end(fam, s, 3.0 * n * sizeof(cpx<T>), 0.0);   // read r, v; write s
 }
 
 template <typename T>
@@ -263,7 +265,9 @@ template <typename T>
 void bicg_xr_update_reduce(laph_ctx *ctx, const RedPlan &pl, long nrows, const BicgScalars &sc, cpx<T> *x,
                            const cpx<T> *p, const cpx<T> *sv, const cpx<T> *t, cpx<T> *r, const cpx<T> *rhat,
                            c64 *red, cudaStream_t s) {
-    run_reduce<2>(ctx, pl, nrows, XRBody<T>{sc, x, p, sv, t, r, rhat}, red, s);
+    // read x, p, s, t, rhat; write x, r
+    run_reduce<2>(ctx, pl, nrows, XRBody<T>{sc, x, p, sv, t, r, rhat}, red, s, nullptr,
+                  7.0 * nrows * pl.nr * sizeof(cpx<T>));
 }
 
 template void bicg_p_update<float>(long, int, const BicgScalars &, const c32 *, c32 *, const c32 *, cudaStream_t);
@@ -274,6 +278,106 @@ template void bicg_xr_update_reduce<float>(laph_ctx *, const RedPlan &, long, co
                                            const c32 *, const c32 *, c32 *, const c32 *, c64 *, cudaStream_t);
 template void bicg_xr_update_reduce<double>(laph_ctx *, const RedPlan &, long, const BicgScalars &, c64 *, const c64 *,
                                             const c64 *, const c64 *, c64 *, const c64 *, c64 *, cudaStream_t);
+
+// ------------------------------------------------------------------ BF16-stored vectors
+// Inner vectors of LAPH_SOLVE_MIXED_BF16: one complex per __nv_bfloat162, FP32 arithmetic; the
+// iterate x stays FP32.  Same element order as the FP32 fields (element i is right-hand side i % nr).
+__device__ __forceinline__ c32 bfl(bf2 v) {
+    const float2 f = __bfloat1622float2(v);
+    return c32{f.x, f.y};
+}
+__device__ __forceinline__ bf2 bfs(c32 v) { return __float22bfloat162_rn(make_float2(v.re, v.im)); }
+
+__global__ void bf_p_update_kernel(long n, int nr, BicgScalars sc, const bf2 *r, bf2 *p, const bf2 *v) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = (int)(i % nr);
+    const c32 b = cvt<float>(sc.beta[k]), w = cvt<float>(sc.omega[k]);
+    p[i] = bfs(bfl(r[i]) + b * (bfl(p[i]) - w * bfl(v[i])));
+}
+void bicg_p_update_bf16(long nrows, int nr, const BicgScalars &sc, const bf2 *r, bf2 *p, const bf2 *v,
+                        cudaStream_t s) {
+    long n = nrows * nr;
+    prof_begin("blas_bf16", s);
+    bf_p_update_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, nr, sc, r, p, v);
+    LAPH_LAUNCH_CHECK();
+    prof_end("blas_bf16", s, 4.0 * n * sizeof(bf2), 0.0);
+}
+
+__global__ void bf_s_update_kernel(long n, int nr, BicgScalars sc, const bf2 *r, const bf2 *v, bf2 *sv) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const c32 a = cvt<float>(sc.alpha[i % nr]);
+    sv[i] = bfs(bfl(r[i]) - a * bfl(v[i]));
+}
+void bicg_s_update_bf16(long nrows, int nr, const BicgScalars &sc, const bf2 *r, const bf2 *v, bf2 *sv,
+                        cudaStream_t s) {
+    long n = nrows * nr;
+    prof_begin("blas_bf16", s);
+    bf_s_update_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, nr, sc, r, v, sv);
+    LAPH_LAUNCH_CHECK();
+    prof_end("blas_bf16", s, 3.0 * n * sizeof(bf2), 0.0);
+}
+
+// conj(a) b summed per right-hand side
+struct BfDots1 {
+    using Acc = c32;
+    const bf2 *a0, *b0;
+    __device__ void operator()(long i, int, Acc *acc) const { acc[0] += cmul_conj(bfl(a0[i]), bfl(b0[i])); }
+    __device__ void two(long i, long j, int k, Acc *acc) const {
+        const c32 ai = bfl(a0[i]), bi = bfl(b0[i]), aj = bfl(a0[j]), bj = bfl(b0[j]);
+        acc[0] += cmul_conj(ai, bi);
+        acc[0] += cmul_conj(aj, bj);
+    }
+};
+// x += alpha p + omega s (x FP32); r = s - omega t stored in BF16; <rhat, r>, <r, r> of the stored r
+struct BfXR {
+    BicgScalars sc;
+    c32 *x;
+    const bf2 *p, *sv, *t;
+    bf2 *r;
+    const bf2 *rhat;
+    using Acc = c32;
+    __device__ void operator()(long i, int k, Acc *acc) const {
+        const c32 a = cvt<float>(sc.alpha[k]), w = cvt<float>(sc.omega[k]);
+        const c32 si = bfl(sv[i]);
+        x[i] = x[i] + a * bfl(p[i]) + w * si;
+        const bf2 rs = bfs(si - w * bfl(t[i]));
+        r[i] = rs;
+        const c32 rn = bfl(rs);
+        acc[0] += cmul_conj(bfl(rhat[i]), rn);
+        acc[1] += cmul_conj(rn, rn);
+    }
+    __device__ void two(long i, long j, int k, Acc *acc) const {
+        (*this)(i, k, acc);
+        (*this)(j, k, acc);
+    }
+};
+
+void mrhs_dots_bf16(laph_ctx *ctx, const RedPlan &pl, long nrows, const bf2 *a, const bf2 *b, c64 *out,
+                    cudaStream_t s) {
+    run_reduce<1>(ctx, pl, nrows, BfDots1{a, b}, out, s, "blas_bf16", 2.0 * nrows * pl.nr * sizeof(bf2));
+}
+void bicg_xr_update_reduce_bf16(laph_ctx *ctx, const RedPlan &pl, long nrows, const BicgScalars &sc, c32 *x,
+                                const bf2 *p, const bf2 *sv, const bf2 *t, bf2 *r, const bf2 *rhat, c64 *red,
+                                cudaStream_t s) {
+    run_reduce<2>(ctx, pl, nrows, BfXR{sc, x, p, sv, t, r, rhat}, red, s, "blas_bf16",
+                  (double)nrows * pl.nr * (5.0 * sizeof(bf2) + 2.0 * sizeof(c32)));
+}
+
+__global__ void bf_from64_kernel(long n, int nr, const double *scale, const c64 *x, bf2 *y) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = scale[i % nr];
+    y[i] = bfs(c32{(float)(a * x[i].re), (float)(a * x[i].im)});
+}
+void mrhs_copy_scaled_bf16(long nrows, int nr, const double *scale, const c64 *x, bf2 *y, cudaStream_t s) {
+    long n = nrows * nr;
+    prof_begin("blas_convert", s);
+    bf_from64_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, nr, scale, x, y);
+    LAPH_LAUNCH_CHECK();
+    prof_end("blas_convert", s, 0.0, 0.0);
+}
 
 __device__ __forceinline__ c64 cdiv(c64 a, c64 b) {
     double d = norm2(b);

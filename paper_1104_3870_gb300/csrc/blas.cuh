@@ -57,6 +57,20 @@ void bicg_xr_update_reduce(laph_ctx *ctx, const RedPlan &pl, long nrows, const B
                            const cpx<T> *p, const cpx<T> *sv, const cpx<T> *t, cpx<T> *r, const cpx<T> *rhat,
                            c64 *red, cudaStream_t s);
 
+// BF16-stored inner vectors (one complex per bf2), FP32 arithmetic, FP32 iterate x.
+using bf2 = __nv_bfloat162;
+void bicg_p_update_bf16(long nrows, int nr, const BicgScalars &sc, const bf2 *r, bf2 *p, const bf2 *v,
+                        cudaStream_t s);
+void bicg_s_update_bf16(long nrows, int nr, const BicgScalars &sc, const bf2 *r, const bf2 *v, bf2 *sv,
+                        cudaStream_t s);
+void bicg_xr_update_reduce_bf16(laph_ctx *ctx, const RedPlan &pl, long nrows, const BicgScalars &sc, cpx<float> *x,
+                                const bf2 *p, const bf2 *sv, const bf2 *t, bf2 *r, const bf2 *rhat, c64 *red,
+                                cudaStream_t s);
+void mrhs_dots_bf16(laph_ctx *ctx, const RedPlan &pl, long nrows, const bf2 *a, const bf2 *b, c64 *out,
+                    cudaStream_t s);
+// y = bf16(scale[r] * x) from an FP64 field
+void mrhs_copy_scaled_bf16(long nrows, int nr, const double *scale, const c64 *x, bf2 *y, cudaStream_t s);
+
 void bicg_init_scalars(int nr, const BicgScalars &sc, const c64 *red_rr, double rel_tol, cudaStream_t s);
 void bicg_alpha(int nr, const BicgScalars &sc, const c64 *red, cudaStream_t s);
 void bicg_omega(int nr, const BicgScalars &sc, const c64 *red, cudaStream_t s);

@@ -32,6 +32,7 @@ struct DiracOp {
     __nv_bfloat16 *cinv16 = nullptr;  // A^{-1} [2][Vh][2][36]
     // FP32 inner-operator operands in packed form (dslash_f32.cu)
     int *nbr = nullptr;       // [2][Vh][8] neighbour table, sign-folded
+    int *order = nullptr;     // [Vh] visiting order of the output sites (z-blocked), see dslash_f32.cu
     float4 *L32w = nullptr;   // [2][4][Vh][9] (re, re, im, im)
     float *C32w = nullptr;    // [2][Vh][2][72] clover inverse
     float *C32wA = nullptr;   // [2][Vh][2][72] clover A (full-lattice K for the learned solver)
@@ -69,9 +70,13 @@ void hop_f32(const DiracOp &op, int p, HopMode mode, cpx<float> *out, const cpx<
 bool hop_f32_xpay_dots(laph_ctx *ctx, const DiracOp &op, int p, cpx<float> *out, const cpx<float> *in,
                        const cpx<float> *z, int nr, cpx<double> *red, cudaStream_t s);
 
-// BF16-stored inner operator: spinors, links and clover inverse in BF16, FP32 arithmetic.
+// BF16-stored spinors ([cb][12][nr] bf162: one complex per element), FP32 links and clover inverse, FP32
+// arithmetic: the copy-engine-fed kernel of hop_f32 reading and writing BF16 tiles.  nr must be 32, 64,
+// 128 or 256.  The xpay form with the fused <out, z>, <out, out> returns false where unavailable.
 void hop_bf16(const DiracOp &op, int p, HopMode mode, __nv_bfloat162 *out, const __nv_bfloat162 *in,
               const __nv_bfloat162 *z, int nr, cudaStream_t s);
+bool hop_bf16_xpay_dots(laph_ctx *ctx, const DiracOp &op, int p, __nv_bfloat162 *out, const __nv_bfloat162 *in,
+                        const __nv_bfloat162 *z, int nr, cpx<double> *red, cudaStream_t s);
 
 // Multiplies a parity half by A_pp^{-1} (T precision).
 template <typename T>

@@ -9,6 +9,7 @@
 // G_4 = 1, so (1 -+ gamma_mu) psi is fixed by the two-spin half h = u -+ G d
 // (u = spins 0,1; d = spins 2,3): upper = h, lower = -+ G^dag h.  Only h is
 // multiplied by the link (two colour vectors instead of four).
+#include "blas.cuh"
 #include "dirac.cuh"
 
 namespace laph {
@@ -381,12 +382,16 @@ extern "C" int laph_dslash_eo(laph_ctx *ctx, const laph_lattice *lat, const void
         LAPH_REQUIRE(parity == 0 || parity == 1, "parity must be 0 or 1");
         LAPH_REQUIRE(mode == LAPH_HOP_CLOVINV || mode == LAPH_HOP_CLOVINV_XPAY || mode == LAPH_HOP_APPLY,
                      "unknown hop mode");
-        LAPH_REQUIRE(precision == LAPH_PREC_FP64 || precision == LAPH_PREC_FP32, "unknown precision");
+        LAPH_REQUIRE(precision == LAPH_PREC_FP64 || precision == LAPH_PREC_FP32 || precision == LAPH_PREC_BF16,
+                     "unknown precision");
+        LAPH_REQUIRE(precision != LAPH_PREC_BF16 || (nrhs >= 32 && nrhs <= 256 && (nrhs & (nrhs - 1)) == 0),
+                     "the BF16 hop takes 32, 64, 128 or 256 right-hand sides");
         LAPH_REQUIRE(nrhs >= 1, "nrhs must be >= 1");
         LAPH_REQUIRE(in != nullptr && out != nullptr, "in/out are null");
         LAPH_REQUIRE(mode == LAPH_HOP_CLOVINV || z != nullptr, "z is required in this mode");
         cudaStream_t s = as_stream(stream);
-        const size_t elem = precision == LAPH_PREC_FP64 ? sizeof(c64) : sizeof(c32);
+        const size_t elem = precision == LAPH_PREC_FP64 ? sizeof(c64) : precision == LAPH_PREC_FP32 ? sizeof(c32)
+                                                                                                   : sizeof(bf2);
         const size_t hb = elem * 12 * g.Vh * nrhs;
         const c64 *L = (const c64 *)stage_in(ctx, links, sizeof(c64) * 36 * g.V, "links", s);
         const void *x = stage_in(ctx, in, hb, "hop_in", s);
@@ -399,8 +404,10 @@ extern "C" int laph_dslash_eo(laph_ctx *ctx, const laph_lattice *lat, const void
             const c64 *zp = (const c64 *)zz;
             hop<double>(op, parity, hm, (c64 *)o.dev, (const c64 *)x, hm == HOP_CLOVINV_XPAY ? zp : nullptr,
                         hm == HOP_APPLY ? zp : nullptr, nrhs, s);
-        } else {
+        } else if (precision == LAPH_PREC_FP32) {
             hop_f32(op, parity, hm, (c32 *)o.dev, (const c32 *)x, (const c32 *)zz, nrhs, s);
+        } else {
+            hop_bf16(op, parity, hm, (bf2 *)o.dev, (const bf2 *)x, (const bf2 *)zz, nrhs, s);
         }
         o.commit(s);
         LAPH_CUDA(cudaStreamSynchronize(s));

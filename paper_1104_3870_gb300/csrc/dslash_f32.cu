@@ -35,6 +35,15 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a
 // operand load: read-only global path (G) or plain load (shared-memory staging)
 template <bool G, typename T>
 __device__ __forceinline__ T ld(const T *p) { return G ? __ldg(p) : *p; }
+// spinor elements: FP32 (float2) or BF16 (bf162) storage, FP32 arithmetic
+__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+__device__ __forceinline__ float2 to_f2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+template <typename E>
+__device__ __forceinline__ E from_f2(float2 v);
+template <>
+__device__ __forceinline__ float2 from_f2<float2>(float2 v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat162 from_f2<__nv_bfloat162>(float2 v) { return __float22bfloat162_rn(v); }
 
 // k[a] = sum_b U[a][b] h[b] (fwd) or sum_b conj(U[b][a]) h[b] (!fwd), two spin components.
 template <bool FWD, bool G = true>
@@ -65,14 +74,14 @@ __device__ __forceinline__ void su3_mul2(const float4 *__restrict__ u, const flo
 
 // One direction: project the neighbour spinor, multiply by the link, accumulate with weight c.
 // FWD: (1 - gamma_mu) U psi(x+mu);  !FWD: (1 + gamma_mu) U^dag psi(x-mu).
-template <int MU, bool FWD, bool G = true>
-__device__ __forceinline__ void hop_dir2(float2 acc[12], const float2 *__restrict__ src, int nr,
+template <int MU, bool FWD, bool G = true, typename E = float2>
+__device__ __forceinline__ void hop_dir2(float2 acc[12], const E *__restrict__ src, int nr,
                                          const float4 *__restrict__ u, float c) {
     float2 h0[3], h1[3];
 #pragma unroll
     for (int col = 0; col < 3; ++col) {
-        float2 u0 = src[(long)(0 * 3 + col) * nr], u1 = src[(long)(1 * 3 + col) * nr];
-        float2 d0 = src[(long)(2 * 3 + col) * nr], d1 = src[(long)(3 * 3 + col) * nr];
+        float2 u0 = to_f2(src[(long)(0 * 3 + col) * nr]), u1 = to_f2(src[(long)(1 * 3 + col) * nr]);
+        float2 d0 = to_f2(src[(long)(2 * 3 + col) * nr]), d1 = to_f2(src[(long)(3 * 3 + col) * nr]);
         // h = u -+ G d with G_1 = -i sigma_1, G_2 = -i sigma_2, G_3 = -i sigma_3, G_4 = 1
         if (MU == 0) {
             h0[col] = FWD ? add2(u0, rot_i(d1)) : sub2(u0, rot_i(d1));
@@ -210,9 +219,9 @@ __global__ void __launch_bounds__(128, MODE == HOP_APPLY ? 6 : 8) hop2_kernel(co
 constexpr int HOP3_WARPS = 4;
 // RPT right-hand sides per lane: a warp owns 32 RPT RHS of its site; the tile of a hop is
 // 12 rows x 256 RPT B, followed by the link (144 B) or the clover block (576 B).
-template <int RPT>
+template <int RPT, typename E = float2>
 struct Hop3Geo {
-    static constexpr int SPIN = 3072 * RPT;
+    static constexpr int SPIN = 12 * 32 * RPT * (int)sizeof(E);     // 3072 RPT B (FP32), 1536 RPT B (BF16)
     static constexpr int SLOT = ((SPIN + 576 + 127) / 128) * 128;   // 128-byte aligned slots
 };
 constexpr long long HOP3_WAIT_CYCLES = 1LL << 31;   // about one second at the maximum SM clock
@@ -222,14 +231,14 @@ __device__ int g_hop3_timeout;   // set when a copy wait gives up (or the ring i
 // DOTS (xpay mode, nr = 32 RPT): the epilogue also accumulates, per right-hand side, the inner
 // products <out, z> and <out, out> of the warp's sites in FP32 and writes them as the warp's
 // partial sums partial[warp][k][r] (k = 0, 1; FP64) for a fixed-order final sum.
-template <int MODE, int NS, int RPT, bool DOTS = false>
+template <int MODE, int NS, int RPT, bool DOTS = false, typename E = float2>
 __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
     hop3_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_z,
-                const int *__restrict__ nbr, const float4 *__restrict__ L, const float *__restrict__ C, int Vh, int p,
-                float hws, float hwt, float2 *__restrict__ out, int nr, int gshift, int nunits,
-                c64 *__restrict__ partial) {
+                const int *__restrict__ nbr, const int *__restrict__ order, const float4 *__restrict__ L,
+                const float *__restrict__ C, int Vh, int p, float hws, float hwt, E *__restrict__ out, int nr, int gshift,
+                int nunits, c64 *__restrict__ partial) {
     extern __shared__ __align__(128) unsigned char sm3[];
-    constexpr int HOP3_SPIN = Hop3Geo<RPT>::SPIN, HOP3_SLOT = Hop3Geo<RPT>::SLOT;
+    constexpr int HOP3_SPIN = Hop3Geo<RPT, E>::SPIN, HOP3_SLOT = Hop3Geo<RPT, E>::SLOT;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (smem_u32(sm3) & 127) {   // tensor copies need 128-byte aligned destinations
         if (threadIdx.x == 0) atomicExch(&g_hop3_timeout, 2);
@@ -253,13 +262,15 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
     // issue pointer: job ij of the unit iq (the ik-th of this warp) goes to slot islot; lane
     // d < 8 holds neighbour d of unit iq (nb_i) and of the unit after it (nb_n)
     int iq = gw, ik = 0, ij = 0, islot = 0, niss = 0;
-    int nb_i = (nu > 0 && lane < 8) ? __ldg(nbp + (iq >> gshift) * 8 + lane) : 0;
-    int nb_n = (nu > 1 && lane < 8) ? __ldg(nbp + ((iq + gstride) >> gshift) * 8 + lane) : 0;
+    // order[u]: the output site (checkerboard index) of the u-th unit site in visiting order
+    int icb = nu > 0 ? __ldg(order + (iq >> gshift)) : 0;
+    int nb_i = (nu > 0 && lane < 8) ? __ldg(nbp + icb * 8 + lane) : 0;
+    int nb_n = (nu > 1 && lane < 8) ? __ldg(nbp + __ldg(order + ((iq + gstride) >> gshift)) * 8 + lane) : 0;
     auto issue = [&]() {
         if (ik >= nu) return;
         const int e = __shfl_sync(0xffffffffu, nb_i, (ij & 1) ? 4 + (ij >> 1) : (ij >> 1));
         if (lane == 0) {
-            const int cb = iq >> gshift, h = iq & gmask;
+            const int cb = icb, h = iq & gmask;
             unsigned char *sl = ring + islot * HOP3_SLOT;
             uint64_t *b = bar + islot;
             fence_proxy_async_smem();
@@ -287,7 +298,8 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
             ++ik;
             iq += gstride;
             nb_i = nb_n;
-            nb_n = (ik + 1 < nu && lane < 8) ? __ldg(nbp + ((iq + gstride) >> gshift) * 8 + lane) : 0;
+            icb = ik < nu ? __ldg(order + (iq >> gshift)) : 0;
+            nb_n = (ik + 1 < nu && lane < 8) ? __ldg(nbp + __ldg(order + ((iq + gstride) >> gshift)) * 8 + lane) : 0;
         }
     };
     // consume pointer
@@ -316,7 +328,7 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
     }
     bool ok = true;
     for (int k = 0, q = gw; k < nu && ok; ++k, q += gstride) {
-        const int cb = q >> gshift, h = q & gmask;
+        const int cb = __ldg(order + (q >> gshift)), h = q & gmask;
         float2 acc[RPT][12];
 #pragma unroll
         for (int q = 0; q < RPT; ++q)
@@ -330,8 +342,8 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
             const unsigned char *sl_ = ring + cslot * HOP3_SLOT;                                           \
             const float c_ = meta[cslot];                                                                  \
             _Pragma("unroll") for (int q = 0; q < RPT; ++q)                                                \
-                hop_dir2<MU, FWD, false>(acc[q], reinterpret_cast<const float2 *>(sl_) + 32 * q + lane,    \
-                                         32 * RPT, reinterpret_cast<const float4 *>(sl_ + HOP3_SPIN), c_); \
+                hop_dir2<MU, FWD, false, E>(acc[q], reinterpret_cast<const E *>(sl_) + 32 * q + lane,      \
+                                            32 * RPT, reinterpret_cast<const float4 *>(sl_ + HOP3_SPIN), c_); \
             release();                                                                                     \
         }                                                                                                  \
     }
@@ -353,11 +365,11 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
         float2 res[RPT][12];
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
-            const float2 *zs = reinterpret_cast<const float2 *>(sl) + 32 * q + lane;
+            const E *zs = reinterpret_cast<const E *>(sl) + 32 * q + lane;
             if (MODE == HOP_APPLY) {
                 float2 xv[12];
 #pragma unroll
-                for (int c = 0; c < 12; ++c) xv[c] = zs[c * 32 * RPT];
+                for (int c = 0; c < 12; ++c) xv[c] = to_f2(zs[c * 32 * RPT]);
                 herm6_f2<false>(cl, xv, res[q]);
                 herm6_f2<false>(cl + 72, xv + 6, res[q] + 6);
 #pragma unroll
@@ -368,7 +380,7 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
                 if (MODE == HOP_CLOVINV_XPAY) {
 #pragma unroll
                     for (int c = 0; c < 12; ++c) {
-                        const float2 zc = zs[c * 32 * RPT];
+                        const float2 zc = to_f2(zs[c * 32 * RPT]);
                         res[q][c] = sub2(zc, res[q][c]);
                         if (DOTS) {   // conj(t) z and |t|^2
                             const float2 t = res[q][c];
@@ -383,9 +395,9 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
         release();
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
-            float2 *dst = out + (long)cb * 12 * nr + 32 * RPT * h + 32 * q + lane;
+            E *dst = out + (long)cb * 12 * nr + 32 * RPT * h + 32 * q + lane;
 #pragma unroll
-            for (int c = 0; c < 12; ++c) dst[(long)c * nr] = res[q][c];
+            for (int c = 0; c < 12; ++c) dst[(long)c * nr] = from_f2<E>(res[q][c]);
         }
     }
     if (DOTS) {   // every warp writes, zeros where it had no units
@@ -412,7 +424,9 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
 
 // 2D view of a half-lattice FP32 field [cb][12][nr] complex: rows (cb, component) of 2 nr
 // floats; a box is the 12 rows x 32 rpt right-hand sides that one warp reads.
-static CUtensorMap spinor_map(const float2 *base, long Vh, int nr, int rpt) {
+template <typename E>
+static CUtensorMap spinor_map(const E *base, long Vh, int nr, int rpt) {
+    constexpr bool bf = sizeof(E) == 4;   // bf162 (two BF16 reals) or float2 (two FP32 reals)
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -423,29 +437,30 @@ static CUtensorMap spinor_map(const float2 *base, long Vh, int nr, int rpt) {
     }
     CUtensorMap m;
     const cuuint64_t dims[2] = {(cuuint64_t)(2 * nr), (cuuint64_t)(12 * Vh)};
-    const cuuint64_t strides[1] = {(cuuint64_t)(2 * nr) * sizeof(float)};
+    const cuuint64_t strides[1] = {(cuuint64_t)(2 * nr) * (bf ? 2 : 4)};
     const cuuint32_t box[2] = {(cuuint32_t)(64 * rpt), 12};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(base), dims, strides, box, estr,
+    CUresult r = encode(&m, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        const_cast<E *>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     LAPH_REQUIRE(r == CUDA_SUCCESS, "tensor map encoding failed");
     return m;
 }
 
-template <int MODE, int NS, int RPT, bool DOTS = false>
-static long launch_hop3(const DiracOp &op, int p, float hws, float hwt, float2 *out, const float2 *in,
-                        const float2 *z, int nr, cudaStream_t s, laph_ctx *ctx = nullptr, c64 *red = nullptr) {
-    constexpr size_t smem = (size_t)HOP3_WARPS * NS * (Hop3Geo<RPT>::SLOT + 8 + 4);
+template <int MODE, int NS, int RPT, bool DOTS = false, typename E = float2>
+static long launch_hop3(const DiracOp &op, int p, float hws, float hwt, E *out, const E *in,
+                        const E *z, int nr, cudaStream_t s, laph_ctx *ctx = nullptr, c64 *red = nullptr) {
+    constexpr size_t smem = (size_t)HOP3_WARPS * NS * (Hop3Geo<RPT, E>::SLOT + 8 + 4);
     static int bpsm[64] = {0};
     static int nsm[64] = {0};
     int dev = 0;
     LAPH_CUDA(cudaGetDevice(&dev));
     LAPH_REQUIRE(dev < 64, "device index out of range");
     if (bpsm[dev] == 0) {
-        LAPH_CUDA(cudaFuncSetAttribute(hop3_kernel<MODE, NS, RPT, DOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-        LAPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm[dev], hop3_kernel<MODE, NS, RPT, DOTS>,
+        LAPH_CUDA(cudaFuncSetAttribute(hop3_kernel<MODE, NS, RPT, DOTS, E>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LAPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm[dev], hop3_kernel<MODE, NS, RPT, DOTS, E>,
                                                                 HOP3_WARPS * 32, smem));
         LAPH_CUDA(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
         LAPH_REQUIRE(bpsm[dev] > 0, "TMA hop kernel does not fit on this device");
@@ -460,8 +475,9 @@ static long launch_hop3(const DiracOp &op, int p, float hws, float hwt, float2 *
     if (grid > cap) grid = cap;
     c64 *partial = nullptr;
     if (DOTS) partial = (c64 *)ws_get(ctx, "hop3:dots", sizeof(c64) * 2 * nr * grid * HOP3_WARPS);
-    hop3_kernel<MODE, NS, RPT, DOTS><<<(unsigned)grid, HOP3_WARPS * 32, smem, s>>>(
-        tin, tz, op.nbr, op.L32w, MODE == HOP_APPLY ? op.C32wA : op.C32w, (int)op.g.Vh, p, hws, hwt, out, nr, gshift,
+    hop3_kernel<MODE, NS, RPT, DOTS, E><<<(unsigned)grid, HOP3_WARPS * 32, smem, s>>>(
+        tin, tz, op.nbr, op.order, op.L32w, MODE == HOP_APPLY ? op.C32wA : op.C32w, (int)op.g.Vh, p, hws, hwt, out, nr,
+        gshift,
         (int)nunits, partial);
     if (DOTS) {
         LAPH_LAUNCH_CHECK();
@@ -499,7 +515,7 @@ static void hop3_modes(const DiracOp &op, int p, HopMode mode, float hws, float 
     if (mode == HOP_APPLY)
         launch_hop3<HOP_APPLY, NS, RPT>(op, p, hws, hwt, out, in, z, nr, s);
     else if (mode == HOP_CLOVINV)
-        launch_hop3<HOP_CLOVINV, NS, RPT>(op, p, hws, hwt, out, in, nullptr, nr, s);
+        launch_hop3<HOP_CLOVINV, NS, RPT>(op, p, hws, hwt, out, in, (const float2 *)nullptr, nr, s);
     else
         launch_hop3<HOP_CLOVINV_XPAY, NS, RPT>(op, p, hws, hwt, out, in, z, nr, s);
 }
@@ -575,6 +591,62 @@ bool hop_f32_xpay_dots(laph_ctx *ctx, const DiracOp &op, int p, c32 *out, const 
     return true;
 }
 
+// ------------------------------------------------------------------ BF16-stored spinors
+// Algorithmic bytes of one BF16 hop launch: spinors 24 BF16 reals (2 B) in and out (and z),
+// the 8 links of a site as 12 FP32 reals and the 72 FP32 clover reals, once per launch.
+static double hop_bytes_bf16(const DiracOp &op, HopMode mode, int nr) {
+    const double spin = 24.0 * 2.0;
+    const double per_rhs = 2.0 * spin + (mode == HOP_CLOVINV ? 0.0 : spin);
+    return (double)op.g.Vh * (nr * per_rhs + 8.0 * 12.0 * 4.0 + 72.0 * 4.0);
+}
+
+static bool bf16_ok(const DiracOp &op, const void *in, const void *z, int nr) {
+    const bool aligned = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(z) |
+                           reinterpret_cast<uintptr_t>(op.L32w) | reinterpret_cast<uintptr_t>(op.C32w) |
+                           reinterpret_cast<uintptr_t>(op.C32wA)) & 15) == 0;
+    return aligned && nr % 32 == 0 && nr >= 32 && nr <= 256 && (nr & (nr - 1)) == 0 &&
+           op.g.Vh * (nr / 32) < (1L << 30);
+}
+
+void hop_bf16(const DiracOp &op, int p, HopMode mode, __nv_bfloat162 *out, const __nv_bfloat162 *in,
+              const __nv_bfloat162 *z, int nr, cudaStream_t s) {
+    LAPH_REQUIRE(mode == HOP_CLOVINV || mode == HOP_CLOVINV_XPAY || mode == HOP_APPLY,
+                 "BF16 hop supports the clover-inverse and apply modes");
+    LAPH_REQUIRE(bf16_ok(op, in, z, nr), "BF16 hop needs 16-byte aligned operands and 32, 64, 128 or 256 "
+                                         "right-hand sides");
+    const float hws = (float)op.hw[0], hwt = (float)op.hw[3];
+    prof_begin("dslash_bf16", s);
+    const bool two = hop3_rpt_max() == 2 && nr % 64 == 0;
+    if (mode == HOP_APPLY)
+        two ? (void)launch_hop3<HOP_APPLY, 2, 2, false>(op, p, hws, hwt, out, in, z, nr, s)
+            : (void)launch_hop3<HOP_APPLY, 2, 1, false>(op, p, hws, hwt, out, in, z, nr, s);
+    else if (mode == HOP_CLOVINV)
+        two ? (void)launch_hop3<HOP_CLOVINV, 2, 2, false>(op, p, hws, hwt, out, in, (const __nv_bfloat162 *)nullptr,
+                                                          nr, s)
+            : (void)launch_hop3<HOP_CLOVINV, 2, 1, false>(op, p, hws, hwt, out, in, (const __nv_bfloat162 *)nullptr,
+                                                          nr, s);
+    else
+        two ? (void)launch_hop3<HOP_CLOVINV_XPAY, 2, 2, false>(op, p, hws, hwt, out, in, z, nr, s)
+            : (void)launch_hop3<HOP_CLOVINV_XPAY, 2, 1, false>(op, p, hws, hwt, out, in, z, nr, s);
+    LAPH_LAUNCH_CHECK();
+    prof_end("dslash_bf16", s, hop_bytes_bf16(op, mode, nr), hop_flops(op, nr));
+}
+
+bool hop_bf16_xpay_dots(laph_ctx *ctx, const DiracOp &op, int p, __nv_bfloat162 *out, const __nv_bfloat162 *in,
+                        const __nv_bfloat162 *z, int nr, c64 *red, cudaStream_t s) {
+    const int rpt = (hop3_rpt_max() == 2 && nr == 64) ? 2 : 1;
+    if (!bf16_ok(op, in, z, nr) || nr != 32 * rpt) return false;
+    const float hws = (float)op.hw[0], hwt = (float)op.hw[3];
+    prof_begin("dslash_bf16", s);
+    if (rpt == 2)
+        launch_hop3<HOP_CLOVINV_XPAY, 2, 2, true>(op, p, hws, hwt, out, in, z, nr, s, ctx, red);
+    else
+        launch_hop3<HOP_CLOVINV_XPAY, 2, 1, true>(op, p, hws, hwt, out, in, z, nr, s, ctx, red);
+    LAPH_LAUNCH_CHECK();
+    prof_end("dslash_bf16", s, hop_bytes_bf16(op, HOP_CLOVINV_XPAY, nr), hop_flops(op, nr));
+    return true;
+}
+
 // ------------------------------------------------------------------ operand preparation
 __global__ void nbr_kernel(Geom g, int *nbr) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -620,6 +692,36 @@ __global__ void clov_w_kernel(long nblk, const double *__restrict__ cinv64, floa
     }
 }
 
+// Visiting order of the output sites of the copy-engine-fed hop: z-blocks of bz planes, and inside
+// a block x (half index) fastest, then y, z, t.  The +-t neighbours of consecutive sites are then
+// bz ns^2 / 2 sites apart instead of a whole slice (ns^3 / 2), which keeps a neighbour tile in L2
+// from its first use to its last (24^3 slices, 32 RHS: 35 MB instead of 108 MB between the two);
+// a block's two boundary planes are read once more (1 + 2 / bz of one pass over the input).
+// bz = ns is the lexicographic order.
+__global__ void order_kernel(Geom g, int bz, int *order) {
+    long u = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= g.Vh) return;
+    const int nxh = g.ns / 2;
+    long v = u;
+    const int xh = (int)(v % nxh); v /= nxh;
+    const int y = (int)(v % g.ns); v /= g.ns;
+    const int zi = (int)(v % bz); v /= bz;
+    const int t = (int)(v % g.nt);
+    const int z = (int)(v / g.nt) * bz + zi;
+    order[u] = (int)((((long)t * g.ns + z) * g.ns + y) * nxh + xh);
+}
+
+static int hop_zblock(const Geom &g) {
+    static int env = -2;
+    if (env == -2) {
+        const char *e = getenv("LAPH_HOP_ZBLOCK");
+        env = e ? atoi(e) : -1;
+    }
+    int bz = env >= 0 ? env : 8;
+    if (bz <= 0 || g.ns % bz != 0) bz = g.ns;
+    return bz;
+}
+
 void prepare_f32_operands(laph_ctx *ctx, DiracOp &op, cudaStream_t s) {
     const Geom &g = op.g;
     LAPH_REQUIRE(g.Vh < (1L << 31), "lattice too large for 32-bit neighbour indices");
@@ -628,6 +730,9 @@ void prepare_f32_operands(laph_ctx *ctx, DiracOp &op, cudaStream_t s) {
     op.C32w = (float *)ws_get(ctx, "dirac:C32w", sizeof(float) * 144 * 2 * g.Vh);
     op.C32wA = (float *)ws_get(ctx, "dirac:C32wA", sizeof(float) * 144 * 2 * g.Vh);
     nbr_kernel<<<grid_for(2 * g.Vh, 256), 256, 0, s>>>(g, op.nbr);
+    LAPH_LAUNCH_CHECK();
+    op.order = (int *)ws_get(ctx, "dirac:order", sizeof(int) * g.Vh);
+    order_kernel<<<grid_for(g.Vh, 256), 256, 0, s>>>(g, hop_zblock(g), op.order);
     LAPH_LAUNCH_CHECK();
     links_w_kernel<<<grid_for(8 * g.Vh * 9, 256), 256, 0, s>>>(8 * g.Vh, op.L64, op.L32w);
     LAPH_LAUNCH_CHECK();

@@ -113,9 +113,87 @@ static InnerStats bicgstab_schur(laph_ctx *ctx, const DiracOp &op, int nr, const
     return st;
 }
 
+// The same BiCGStab with every Krylov vector stored in BF16 (one complex per bf2) and FP32
+// arithmetic (LAPH_SOLVE_MIXED_BF16); the iterate x is FP32.  nr must be 32, 64, 128 or 256 (the
+// copy-engine-fed stencil).  Rounding each stored vector to 8 significant bits separates the
+// recursive residual from the true one by about 1e-3 of the starting residual, which the FP64
+// defect correction around this solve absorbs.
+static InnerStats bicgstab_schur_bf16(laph_ctx *ctx, const DiracOp &op, int nr, const bf2 *b, c32 *x,
+                                      double rel_tol, int maxiter, int check_every, cudaStream_t s) {
+    const Geom &g = op.g;
+    long nrows = g.Vh * 12;
+    size_t vb = sizeof(bf2) * nrows * nr;
+    auto V = [&](const char *n) { return (bf2 *)ws_get(ctx, std::string("in16") + n, vb); };
+    bf2 *r = V(":r"), *rh = V(":rh"), *p = V(":p"), *v = V(":v"), *sv = V(":s"), *t = V(":t"), *tmp = V(":tmp");
+    char *scb = (char *)ws_get(ctx, "in16:sc", (sizeof(c64) * 4 + sizeof(double) * 2 + sizeof(int) * 3) * nr + 256);
+    BicgScalars sc;
+    sc.rho = (c64 *)scb;
+    sc.alpha = sc.rho + nr;
+    sc.omega = sc.alpha + nr;
+    sc.beta = sc.omega + nr;
+    sc.rr = (double *)(sc.beta + nr);
+    sc.rr_stop = sc.rr + nr;
+    sc.active = (int *)(sc.rr_stop + nr);
+    sc.status = sc.active + nr;
+    sc.iters = sc.status + nr;
+    c64 *red = (c64 *)ws_get(ctx, "in16:red", sizeof(c64) * 3 * nr);
+    RedPlan pl = red_plan(ctx, nrows, nr);
+
+    LAPH_CUDA(cudaMemsetAsync(x, 0, sizeof(c32) * nrows * nr, s));
+    LAPH_CUDA(cudaMemsetAsync(p, 0, vb, s));
+    LAPH_CUDA(cudaMemsetAsync(v, 0, vb, s));
+    LAPH_CUDA(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, s));
+    LAPH_CUDA(cudaMemcpyAsync(rh, b, vb, cudaMemcpyDeviceToDevice, s));
+    mrhs_dots_bf16(ctx, pl, nrows, r, r, red, s);
+    bicg_init_scalars(nr, sc, red, rel_tol, s);
+
+    int *h_flags = (int *)pinned_get(ctx, sizeof(int) * 3 * nr);
+    if (check_every < 1) check_every = 5;
+    for (int it = 0; it < maxiter; ++it) {
+        bicg_p_update_bf16(nrows, nr, sc, r, p, v, s);
+        hop_bf16(op, 1, HOP_CLOVINV, tmp, p, nullptr, nr, s);          // v = M p
+        hop_bf16(op, 0, HOP_CLOVINV_XPAY, v, tmp, p, nr, s);
+        mrhs_dots_bf16(ctx, pl, nrows, rh, v, red, s);
+        bicg_alpha(nr, sc, red, s);
+        bicg_s_update_bf16(nrows, nr, sc, r, v, sv, s);
+        hop_bf16(op, 1, HOP_CLOVINV, tmp, sv, nullptr, nr, s);         // t = M s, <t, s>, <t, t>
+        if (!hop_bf16_xpay_dots(ctx, op, 0, t, tmp, sv, nr, red, s)) {
+            hop_bf16(op, 0, HOP_CLOVINV_XPAY, t, tmp, sv, nr, s);
+            mrhs_dots_bf16(ctx, pl, nrows, t, sv, red, s);
+            mrhs_dots_bf16(ctx, pl, nrows, t, t, red + nr, s);
+        }
+        bicg_omega(nr, sc, red, s);
+        bicg_xr_update_reduce_bf16(ctx, pl, nrows, sc, x, p, sv, t, r, rh, red, s);
+        bicg_rho(nr, sc, red, s);
+        if ((it + 1) % check_every == 0 || it + 1 == maxiter) {
+            LAPH_CUDA(cudaMemcpyAsync(h_flags, sc.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, s));
+            LAPH_CUDA(cudaStreamSynchronize(s));
+            hop_timeout_check(s);
+            bool any = false;
+            for (int k = 0; k < nr; ++k) any |= h_flags[k] != 0;
+            if (!any) break;
+        }
+    }
+    InnerStats st;
+    st.iters.resize(nr);
+    st.status.resize(nr);
+    LAPH_CUDA(cudaMemcpyAsync(h_flags, sc.iters, sizeof(int) * nr, cudaMemcpyDeviceToHost, s));
+    LAPH_CUDA(cudaMemcpyAsync(h_flags + nr, sc.status, sizeof(int) * nr, cudaMemcpyDeviceToHost, s));
+    LAPH_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < nr; ++k) {
+        st.iters[k] = h_flags[k];
+        st.status[k] = h_flags[nr + k];
+    }
+    return st;
+}
+
 std::vector<int> cgnr_solve(laph_ctx *ctx, const DiracOp &op, int nr, c64 *r, c64 *e,
                             const std::vector<double> &target, int maxiter, int check_every, std::vector<int> &conv,
                             cudaStream_t s);
+
+// Blocks of the BF16 inner solver: the copy-engine-fed stencil's right-hand-side counts.  Other
+// blocks (a short tail) run the FP32 inner solver.
+static bool bf16_block_ok(int nr) { return nr == 32 || nr == 64 || nr == 128 || nr == 256; }
 
 // Solves one block of nr right-hand sides, columns [first, first+nr) of the ABI arrays.
 // A right-hand side still above the tolerance when the inner budget or the cycle limit is
@@ -247,6 +325,13 @@ void solve_block(laph_ctx *ctx, const DiracOp &op, const c64 *rhs, c64 *sol, int
             double want = std::max(1e-15, 0.2 * tol / std::max(worst, tol));
             st = bicgstab_schur<double>(ctx, op, nr, rin, dx, want, budget, prm.check_every, s, "in64");
             mrhs_axpy_scaled<double, double>(nrows, nr, scale + nr, dx, xe, s);
+        } else if (prm.mode == LAPH_SOLVE_MIXED_BF16 && bf16_block_ok(nr)) {
+            bf2 *rin = (bf2 *)ws_get(ctx, "dc:rin16", sizeof(bf2) * nrows * nr);
+            c32 *dx = (c32 *)ws_get(ctx, "dc:dx32", sizeof(c32) * nrows * nr);
+            mrhs_copy_scaled_bf16(nrows, nr, scale, re, rin, s);
+            double want = std::max(prm.inner_tol, 0.2 * tol / std::max(worst, tol));
+            st = bicgstab_schur_bf16(ctx, op, nr, rin, dx, want, budget, prm.check_every, s);
+            mrhs_axpy_scaled<float, double>(nrows, nr, scale + nr, dx, xe, s);
         } else {
             c32 *rin = (c32 *)ws_get(ctx, "dc:rin32", sizeof(c32) * nrows * nr);
             c32 *dx = (c32 *)ws_get(ctx, "dc:dx32", sizeof(c32) * nrows * nr);
@@ -385,11 +470,11 @@ extern "C" int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const v
         if (params) prm = *params;
         if (!(prm.tol > 0.0)) prm.tol = 1e-10;
         if (prm.maxiter <= 0) prm.maxiter = 100000;
-        if (!(prm.inner_tol > 0.0)) prm.inner_tol = 3e-4;
+        if (!(prm.inner_tol > 0.0)) prm.inner_tol = prm.mode == LAPH_SOLVE_MIXED_BF16 ? 1e-2 : 3e-4;
         if (prm.check_every <= 0) prm.check_every = 5;
         LAPH_REQUIRE(prm.mode == LAPH_SOLVE_PLAIN_FP64 || prm.mode == LAPH_SOLVE_MIXED_FP32 ||
-                         prm.mode == LAPH_SOLVE_LEARNED,
-                     "solver mode not available in this build");
+                         prm.mode == LAPH_SOLVE_MIXED_BF16 || prm.mode == LAPH_SOLVE_LEARNED,
+                     "unknown solver mode");
         LAPH_REQUIRE(prm.mode != LAPH_SOLVE_LEARNED || prm.weights != nullptr, "learned mode needs weights");
         if (nrhs == 0) return;
         cudaStream_t s = as_stream(stream);
@@ -405,8 +490,9 @@ extern "C" int dirac_solve_batch(laph_ctx *ctx, const laph_lattice *lat, const v
         int blk = prm.rhs_block;
         if (blk <= 0)
             blk = prm.mode == LAPH_SOLVE_PLAIN_FP64 ? 1
-                  : prm.mode == LAPH_SOLVE_MIXED_FP32 ? autotune_block(ctx, op, nrhs, s)
-                                                      : std::min(nrhs, 64);
+                  : prm.mode == LAPH_SOLVE_MIXED_FP32 || prm.mode == LAPH_SOLVE_MIXED_BF16
+                      ? autotune_block(ctx, op, nrhs, s)
+                      : std::min(nrhs, 64);
         blk = std::min(blk, std::min(nrhs, 256));
         std::vector<laph_solve_report> rep(nrhs);
         for (int first = 0; first < nrhs; first += blk) {

@@ -22,7 +22,7 @@ PLAIN_FP64, MIXED_FP32, MIXED_BF16, LEARNED = range(4)
 CH_PION, CH_RHO, CH_SCALAR, CH_PIPI_I2 = range(4)
 DIL_NONE, DIL_FULL, DIL_BLOCK, DIL_INTERLACE = range(4)
 HOP_CLOVINV, HOP_CLOVINV_XPAY, HOP_APPLY = range(3)
-PREC_FP64, PREC_FP32 = range(2)
+PREC_FP64, PREC_FP32, PREC_BF16 = range(3)
 
 
 class LaphError(RuntimeError):

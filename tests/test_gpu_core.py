@@ -86,6 +86,29 @@ def test_solve_vs_dense_lu(tiny, mode):
         assert reps[i].iters > 0
 
 
+@pytest.mark.parametrize("nrhs,block", [(32, 32), (40, 32)])
+def test_solve_bf16_vs_dense_lu(tiny, nrhs, block):
+    """LAPH_SOLVE_MIXED_BF16: FP64 defect correction around the BF16-stored inner BiCGStab.  The
+    FP64 true residual decides convergence, so the solutions meet the same bounds as the other
+    modes (residual <= 1e-10, LU distance <= 1e-8).  40 sources in blocks of 32: the tail block of
+    8 runs the FP32 inner solver."""
+    L = lib()
+    wl = tiny.wl
+    b = synth.random_spinor(wl.ns, wl.nt, seed=58, nrhs=nrhs)
+    x_lu, _ = tiny.solve(b, "lu")
+    sol = empty(b.shape, dev(b).dtype)
+    prm = L.solver_params(tol=1e-10, mode=L.MIXED_BF16, rhs_block=block)
+    reps = L.dirac_solve_batch(context(), L.lattice(wl.ns, wl.nt, wl.xi), dev(tiny.u), wl.m0, wl.csw, dev(b), sol,
+                               nrhs, prm)
+    x = host(sol)
+    fk = FastK(tiny.K)
+    for i in range(nrhs):
+        assert reps[i].status == 0 and reps[i].true_resid <= 1e-10 and reps[i].fallback_used == 0
+        res = np.linalg.norm(b[i] - fk.apply(x[i])) / np.linalg.norm(b[i])
+        assert res <= 1.05e-10
+        assert np.linalg.norm(x[i] - x_lu[i]) / np.linalg.norm(x_lu[i]) < 1e-8
+
+
 @pytest.mark.parametrize("mode", ["plain", "mixed"])
 def test_solve_cg_fallback(tiny, mode):
     """A Krylov budget far too small for BiCGStab (a host-side injected failure) hands every

@@ -110,7 +110,85 @@ def test_hop_rejects_bad_arguments(lattice):
     x = torch.zeros((vh, 12, 2), dtype=torch.complex128, device="cuda")
     out = torch.empty_like(x)
     lat = L.lattice(ns, nt, XI)
-    for parity, mode, prec, z in ((2, 0, 0, None), (0, 3, 0, None), (0, 0, 2, None), (0, 1, 0, None)):
+    for parity, mode, prec, z in ((2, 0, 0, None), (0, 3, 0, None), (0, 0, 3, None), (0, 1, 0, None),
+                                  (0, 0, 2, None)):   # the last: BF16 with 2 right-hand sides
         with pytest.raises(L.LaphError) as e:
             L.laph_dslash_eo(context(), lat, dev(u), M0, CSW, parity, mode, prec, x, z, out, 2)
         assert e.value.code == L.LAPH_ERR_ARG
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("nr", [32, 64, 128])
+def test_hop_parity_bf16(lattice, mode, nr):
+    """BF16-stored spinors (the inner operator of LAPH_SOLVE_MIXED_BF16): the inputs are rounded
+    to BF16 before the reference sees them, links, clover and arithmetic are FP32, and the output
+    is rounded to BF16 (8 significant bits: unit roundoff 2^-8 per element).  Bound: every
+    element within 2^-8 |ref| + 2e-5 max|ref|, and rel <= 3e-3 in norm."""
+    import torch
+    L = lib()
+    ns, nt, u, K = lattice
+    vh = ns ** 3 * nt // 2
+    rng = np.random.default_rng(2000 + nr)
+
+    def bf(a):
+        return torch.from_numpy(a).to(torch.bfloat16).cuda()
+
+    def cplx(t):
+        f = t.float().cpu().numpy().astype(np.float64)
+        return f[..., 0] + 1j * f[..., 1]
+
+    xb, zb = bf(rng.standard_normal((vh, 12, nr, 2))), bf(rng.standard_normal((vh, 12, nr, 2)))
+    xin, zin = cplx(xb), cplx(zb)
+    for p in (0, 1):
+        out = torch.empty((vh, 12, nr, 2), dtype=torch.bfloat16, device="cuda")
+        L.laph_dslash_eo(context(), L.lattice(ns, nt, XI), dev(u), M0, CSW, p, MODES[mode], L.PREC_BF16, xb,
+                         None if mode == "clovinv" else zb, out, nr)
+        torch.cuda.synchronize()
+        got = cplx(out)
+        ref = reference(K, ns, nt, p, mode, xin, zin)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 3e-3, p
+        assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 2e-5 * np.abs(ref).max()), p
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("mode", ["clovinv", "xpay"])
+@pytest.mark.parametrize("nr", [32, 64])
+def test_hop_parity_zblocked_order(prec, mode, nr):
+    """16^3 x 4: the copy-engine-fed kernel visits the output sites in z-blocks of 8 planes
+    (two blocks here; on the 4^3 and 6^3 lattices above the order is lexicographic).  Same
+    tolerances as the FP32 and BF16 tests above."""
+    import torch
+    L = lib()
+    ns, nt = 16, 4
+    u = gauge.stout(synth.random_su3_field(ns, nt, seed=72), 0.1, 2, spatial_only=False)
+    K = WilsonClover(u, M0, CSW, XI)
+    vh = ns ** 3 * nt // 2
+    rng = np.random.default_rng(3000 + nr)
+    shape = (vh, 12, nr, 2)
+    if prec == "fp32":
+        xt = torch.from_numpy(rng.standard_normal(shape).astype(np.float32)).cuda()
+        zt = torch.from_numpy(rng.standard_normal(shape).astype(np.float32)).cuda()
+        out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    else:
+        xt = torch.from_numpy(rng.standard_normal(shape)).to(torch.bfloat16).cuda()
+        zt = torch.from_numpy(rng.standard_normal(shape)).to(torch.bfloat16).cuda()
+        out = torch.empty(shape, dtype=torch.bfloat16, device="cuda")
+
+    def cplx(t):
+        f = t.float().cpu().numpy().astype(np.float64)
+        return f[..., 0] + 1j * f[..., 1]
+
+    xin, zin = cplx(xt), cplx(zt)
+    for p in (0, 1):
+        L.laph_dslash_eo(context(), L.lattice(ns, nt, XI), dev(u), M0, CSW, p, MODES[mode],
+                         L.PREC_FP32 if prec == "fp32" else L.PREC_BF16, xt, None if mode == "clovinv" else zt,
+                         out, nr)
+        torch.cuda.synchronize()
+        got = cplx(out)
+        ref = reference(K, ns, nt, p, mode, xin, zin)
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        if prec == "fp32":
+            assert rel <= 5e-6 and np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max(), (p, rel)
+        else:
+            assert rel <= 3e-3, (p, rel)
+            assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 2e-5 * np.abs(ref).max()), p
