@@ -219,10 +219,14 @@ __global__ void __launch_bounds__(128, MODE == HOP_APPLY ? 6 : 8) hop2_kernel(co
 constexpr int HOP3_WARPS = 4;
 // RPT right-hand sides per lane: a warp owns 32 RPT RHS of its site; the tile of a hop is
 // 12 rows x 256 RPT B, followed by the link (144 B) or the clover block (576 B).
-template <int RPT, typename E = float2>
+// HPJ hops per job: 1, or 2 (the forward and backward hop of one direction: two tiles and two links
+// per slot, five jobs per site instead of nine, each covering twice the copy latency).
+template <int RPT, typename E = float2, int HPJ = 1>
 struct Hop3Geo {
     static constexpr int SPIN = 12 * 32 * RPT * (int)sizeof(E);     // 3072 RPT B (FP32), 1536 RPT B (BF16)
-    static constexpr int SLOT = ((SPIN + 576 + 127) / 128) * 128;   // 128-byte aligned slots
+    static constexpr int BODY = HPJ * (SPIN + 144) > SPIN + 576 ? HPJ * (SPIN + 144) : SPIN + 576;
+    static constexpr int SLOT = ((BODY + 127) / 128) * 128;         // 128-byte aligned slots
+    static constexpr int JOBS = 8 / HPJ + 1;                        // hop jobs + the epilogue job
 };
 constexpr long long HOP3_WAIT_CYCLES = 1LL << 31;   // about one second at the maximum SM clock
 
@@ -231,14 +235,15 @@ __device__ int g_hop3_timeout;   // set when a copy wait gives up (or the ring i
 // DOTS (xpay mode, nr = 32 RPT): the epilogue also accumulates, per right-hand side, the inner
 // products <out, z> and <out, out> of the warp's sites in FP32 and writes them as the warp's
 // partial sums partial[warp][k][r] (k = 0, 1; FP64) for a fixed-order final sum.
-template <int MODE, int NS, int RPT, bool DOTS = false, typename E = float2>
-__global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
+template <int MODE, int NS, int RPT, bool DOTS = false, typename E = float2, int HPJ = 1>
+__global__ void __launch_bounds__(HOP3_WARPS * 32, 4)
     hop3_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_z,
                 const int *__restrict__ nbr, const int *__restrict__ order, const float4 *__restrict__ L,
                 const float *__restrict__ C, int Vh, int p, float hws, float hwt, E *__restrict__ out, int nr, int gshift,
                 int nunits, c64 *__restrict__ partial) {
     extern __shared__ __align__(128) unsigned char sm3[];
-    constexpr int HOP3_SPIN = Hop3Geo<RPT, E>::SPIN, HOP3_SLOT = Hop3Geo<RPT, E>::SLOT;
+    constexpr int HOP3_SPIN = Hop3Geo<RPT, E, HPJ>::SPIN, HOP3_SLOT = Hop3Geo<RPT, E, HPJ>::SLOT;
+    constexpr int NJ = Hop3Geo<RPT, E, HPJ>::JOBS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (smem_u32(sm3) & 127) {   // tensor copies need 128-byte aligned destinations
         if (threadIdx.x == 0) atomicExch(&g_hop3_timeout, 2);
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
     }
     unsigned char *ring = sm3 + warp * NS * HOP3_SLOT;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm3 + HOP3_WARPS * NS * HOP3_SLOT) + warp * NS;
-    float *meta = reinterpret_cast<float *>(sm3 + HOP3_WARPS * NS * (HOP3_SLOT + 8)) + warp * NS;
+    float *meta = reinterpret_cast<float *>(sm3 + HOP3_WARPS * NS * (HOP3_SLOT + 8)) + warp * NS * 2;
     if (lane < NS) mbar_init(bar + lane, 1);
     mbar_fence_init();
     __syncwarp();
@@ -268,22 +273,35 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
     int nb_n = (nu > 1 && lane < 8) ? __ldg(nbp + __ldg(order + ((iq + gstride) >> gshift)) * 8 + lane) : 0;
     auto issue = [&]() {
         if (ik >= nu) return;
-        const int e = __shfl_sync(0xffffffffu, nb_i, (ij & 1) ? 4 + (ij >> 1) : (ij >> 1));
+        // HPJ = 1: job ij is hop ij of (forward mu = 0, backward mu = 0, forward mu = 1, ...);
+        // HPJ = 2: job ij holds the forward and the backward hop of mu = ij
+        const int e = __shfl_sync(0xffffffffu, nb_i, HPJ == 2 ? ij : ((ij & 1) ? 4 + (ij >> 1) : (ij >> 1)));
+        const int e2 = HPJ == 2 ? __shfl_sync(0xffffffffu, nb_i, 4 + (ij & 3)) : 0;
         if (lane == 0) {
             const int cb = icb, h = iq & gmask;
             unsigned char *sl = ring + islot * HOP3_SLOT;
             uint64_t *b = bar + islot;
             fence_proxy_async_smem();
-            if (ij < 8) {
-                const int mu = ij >> 1;
+            if (ij < NJ - 1) {
+                const int mu = HPJ == 2 ? ij : ij >> 1;
                 const float w = mu == 3 ? hwt : hws;
                 const int jn = e < 0 ? ~e : e;
-                meta[islot] = e < 0 ? -w : w;
-                mbar_arrive_expect_tx(b, HOP3_SPIN + 144);
-                tma_tile_2d(sl, &tm_in, 64 * RPT * h, 12 * jn, b);
-                const float4 *u = (ij & 1) ? L + ((long)((1 - p) * 4 + mu) * Vh + jn) * 9
-                                           : L + ((long)(p * 4 + mu) * Vh + cb) * 9;
-                bulk_g2s(sl + HOP3_SPIN, u, 144, b);
+                meta[2 * islot] = e < 0 ? -w : w;
+                if (HPJ == 2) {
+                    const int jb = e2 < 0 ? ~e2 : e2;
+                    meta[2 * islot + 1] = e2 < 0 ? -w : w;
+                    mbar_arrive_expect_tx(b, 2 * (HOP3_SPIN + 144));
+                    tma_tile_2d(sl, &tm_in, 64 * RPT * h, 12 * jn, b);
+                    tma_tile_2d(sl + HOP3_SPIN, &tm_in, 64 * RPT * h, 12 * jb, b);
+                    bulk_g2s(sl + 2 * HOP3_SPIN, L + ((long)(p * 4 + mu) * Vh + cb) * 9, 144, b);
+                    bulk_g2s(sl + 2 * HOP3_SPIN + 144, L + ((long)((1 - p) * 4 + mu) * Vh + jb) * 9, 144, b);
+                } else {
+                    mbar_arrive_expect_tx(b, HOP3_SPIN + 144);
+                    tma_tile_2d(sl, &tm_in, 64 * RPT * h, 12 * jn, b);
+                    const float4 *u = (ij & 1) ? L + ((long)((1 - p) * 4 + mu) * Vh + jn) * 9
+                                               : L + ((long)(p * 4 + mu) * Vh + cb) * 9;
+                    bulk_g2s(sl + HOP3_SPIN, u, 144, b);
+                }
             } else {
                 constexpr bool needz = MODE != HOP_CLOVINV;
                 mbar_arrive_expect_tx(b, (needz ? HOP3_SPIN : 0) + 576);
@@ -293,7 +311,7 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
         }
         ++niss;
         if (++islot == NS) islot = 0;
-        if (++ij == 9) {
+        if (++ij == NJ) {
             ij = 0;
             ++ik;
             iq += gstride;
@@ -340,22 +358,48 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, RPT == 2 ? 4 : 1)
             ok = false;                                                                                    \
         } else {                                                                                           \
             const unsigned char *sl_ = ring + cslot * HOP3_SLOT;                                           \
-            const float c_ = meta[cslot];                                                                  \
+            const float c_ = meta[2 * cslot];                                                              \
             _Pragma("unroll") for (int q = 0; q < RPT; ++q)                                                \
                 hop_dir2<MU, FWD, false, E>(acc[q], reinterpret_cast<const E *>(sl_) + 32 * q + lane,      \
                                             32 * RPT, reinterpret_cast<const float4 *>(sl_ + HOP3_SPIN), c_); \
             release();                                                                                     \
         }                                                                                                  \
     }
-        HOP3_DIR(0, true)
-        HOP3_DIR(0, false)
-        HOP3_DIR(1, true)
-        HOP3_DIR(1, false)
-        HOP3_DIR(2, true)
-        HOP3_DIR(2, false)
-        HOP3_DIR(3, true)
-        HOP3_DIR(3, false)
+#define HOP3_PAIR(MU)                                                                                      \
+    if (ok) {                                                                                              \
+        if (!wait()) {                                                                                     \
+            ok = false;                                                                                    \
+        } else {                                                                                           \
+            const unsigned char *sl_ = ring + cslot * HOP3_SLOT;                                           \
+            const float cf_ = meta[2 * cslot], cb_ = meta[2 * cslot + 1];                                  \
+            const float4 *lk_ = reinterpret_cast<const float4 *>(sl_ + 2 * HOP3_SPIN);                     \
+            _Pragma("unroll") for (int q = 0; q < RPT; ++q) {                                              \
+                hop_dir2<MU, true, false, E>(acc[q], reinterpret_cast<const E *>(sl_) + 32 * q + lane,     \
+                                             32 * RPT, lk_, cf_);                                          \
+                hop_dir2<MU, false, false, E>(acc[q],                                                      \
+                                              reinterpret_cast<const E *>(sl_ + HOP3_SPIN) + 32 * q + lane, \
+                                              32 * RPT, lk_ + 9, cb_);                                     \
+            }                                                                                              \
+            release();                                                                                     \
+        }                                                                                                  \
+    }
+        if (HPJ == 2) {
+            HOP3_PAIR(0)
+            HOP3_PAIR(1)
+            HOP3_PAIR(2)
+            HOP3_PAIR(3)
+        } else {
+            HOP3_DIR(0, true)
+            HOP3_DIR(0, false)
+            HOP3_DIR(1, true)
+            HOP3_DIR(1, false)
+            HOP3_DIR(2, true)
+            HOP3_DIR(2, false)
+            HOP3_DIR(3, true)
+            HOP3_DIR(3, false)
+        }
 #undef HOP3_DIR
+#undef HOP3_PAIR
         if (!ok || !wait()) {
             ok = false;
             break;
@@ -451,16 +495,18 @@ static CUtensorMap spinor_map(const E *base, long Vh, int nr, int rpt) {
 template <int MODE, int NS, int RPT, bool DOTS = false, typename E = float2>
 static long launch_hop3(const DiracOp &op, int p, float hws, float hwt, E *out, const E *in,
                         const E *z, int nr, cudaStream_t s, laph_ctx *ctx = nullptr, c64 *red = nullptr) {
-    constexpr size_t smem = (size_t)HOP3_WARPS * NS * (Hop3Geo<RPT, E>::SLOT + 8 + 4);
+    // one RHS per lane: two hops per job (the slot still leaves room for four blocks per SM)
+    constexpr int HPJ = RPT == 1 ? 2 : 1;
+    constexpr size_t smem = (size_t)HOP3_WARPS * NS * (Hop3Geo<RPT, E, HPJ>::SLOT + 8 + 8);
     static int bpsm[64] = {0};
     static int nsm[64] = {0};
     int dev = 0;
     LAPH_CUDA(cudaGetDevice(&dev));
     LAPH_REQUIRE(dev < 64, "device index out of range");
     if (bpsm[dev] == 0) {
-        LAPH_CUDA(cudaFuncSetAttribute(hop3_kernel<MODE, NS, RPT, DOTS, E>,
+        LAPH_CUDA(cudaFuncSetAttribute(hop3_kernel<MODE, NS, RPT, DOTS, E, HPJ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        LAPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm[dev], hop3_kernel<MODE, NS, RPT, DOTS, E>,
+        LAPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm[dev], hop3_kernel<MODE, NS, RPT, DOTS, E, HPJ>,
                                                                 HOP3_WARPS * 32, smem));
         LAPH_CUDA(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
         LAPH_REQUIRE(bpsm[dev] > 0, "TMA hop kernel does not fit on this device");
@@ -475,7 +521,7 @@ static long launch_hop3(const DiracOp &op, int p, float hws, float hwt, E *out, 
     if (grid > cap) grid = cap;
     c64 *partial = nullptr;
     if (DOTS) partial = (c64 *)ws_get(ctx, "hop3:dots", sizeof(c64) * 2 * nr * grid * HOP3_WARPS);
-    hop3_kernel<MODE, NS, RPT, DOTS, E><<<(unsigned)grid, HOP3_WARPS * 32, smem, s>>>(
+    hop3_kernel<MODE, NS, RPT, DOTS, E, HPJ><<<(unsigned)grid, HOP3_WARPS * 32, smem, s>>>(
         tin, tz, op.nbr, op.order, op.L32w, MODE == HOP_APPLY ? op.C32wA : op.C32w, (int)op.g.Vh, p, hws, hwt, out, nr,
         gshift,
         (int)nunits, partial);

@@ -4,6 +4,8 @@
 // One GEMM per time slice: (nv x 3 V3) conj-transposed eigenvectors times the
 // (3 V3 x 4 nrhs) solution columns.  FP64, shared-memory tiled: a block owns a
 // 16 (n) x 32 (i, alpha) tile and walks the 3 V3 reduction in 32-wide slabs.
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace laph {
@@ -73,6 +75,21 @@ void sinks(const Geom &g, int nv, int nrhs, const c64 *ev, const c64 *sol, c64 *
     prof_end("sinks", s, 0.0, 8.0 * nv * (double)ncol * 3.0 * g.V3 * g.nt);
 }
 
+void sinks_tensor_core(laph_ctx *ctx, const Geom &g, const c64 *V, int nv, const c64 *X, int nrhs, c64 *coef,
+                       cudaStream_t s);
+void sinks_tc_check(cudaStream_t s);
+
+// LAPH_SINKS_FP64=1 selects the FP64 CUDA-core kernel above instead of the tensor-core one
+// (sinks_tc.cu), for comparisons.
+static bool sinks_fp64_forced() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("LAPH_SINKS_FP64");
+        v = (e && atoi(e) == 1) ? 1 : 0;
+    }
+    return v == 1;
+}
+
 }  // namespace laph
 
 using namespace laph;
@@ -90,7 +107,12 @@ extern "C" int laph_sinks(laph_ctx *ctx, const laph_lattice *lat, const void *ev
         const c64 *ev = (const c64 *)stage_in(ctx, evecs, sizeof(c64) * 3 * g.V3 * g.nt * (size_t)nv, "evecs", s);
         const c64 *x = (const c64 *)stage_in(ctx, sol, sizeof(c64) * 12 * g.V * (size_t)nrhs, "sinks_sol", s);
         StagedOut o = stage_out(ctx, coef, sizeof(c64) * (size_t)nrhs * g.nt * 4 * nv, "coef");
-        sinks(g, nv, nrhs, ev, x, (c64 *)o.dev, s);
+        if (sinks_fp64_forced()) {
+            sinks(g, nv, nrhs, ev, x, (c64 *)o.dev, s);
+        } else {
+            sinks_tensor_core(ctx, g, ev, nv, x, nrhs, (c64 *)o.dev, s);
+            sinks_tc_check(s);
+        }
         o.commit(s);
     });
 }
