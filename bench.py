@@ -77,6 +77,9 @@ def parse_args(argv=None):
     p.add_argument("--dslash-prec", default="fp32,fp64", help="precisions of the Dslash sweep")
     p.add_argument("--dslash-direct", action="store_true",
                    help="time laph_dslash_eo launches alone (clover-inverse mode) instead of inside solver iterations")
+    p.add_argument("--dslash-nt", type=int, default=0,
+                   help="time extent of the Dslash sweep's lattice (0: the workload's); the spatial extent stays the "
+                        "workload's, so a short slab keeps an ncu capture to a few GB on the device")
     return p.parse_args(argv)
 
 
@@ -206,7 +209,7 @@ def oracle_sample(wl, seconds=15.0, threads=None, _cache={}):
 
 
 # ----------------------------------------------------------------------------- ncu traffic record
-HOP_KERNEL_VERSION = "hop3_tma_ns2_zblock8"
+HOP_KERNEL_VERSION = "hop3_tma_ns2_zblock8_pair"
 
 
 def measured_traffic_ratio(workload, family="dslash_fp32"):
@@ -936,6 +939,9 @@ def run_dslash_sweep(args):
     import synth
 
     wl = synth.WORKLOADS[args.workload]
+    if args.dslash_nt > 0:   # a slab of the workload's slices: same spatial extent, fewer slices
+        import dataclasses
+        wl = dataclasses.replace(wl, nt=args.dslash_nt)
     spec = LatticeSpec(wl.ns, wl.nt, wl.xi, wl.m0, wl.csw, wl.nv, (wl.dil_time, wl.dil_spin, wl.dil_laph),
                        wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
     path = LapHPath(spec, 0)
@@ -972,7 +978,7 @@ def run_dslash_sweep(args):
                                     else "hop2_kernel" if prec == "fp32" else "hop_kernel<double>")})
             del b, x
     print(json.dumps({"metric": "Dslash HBM GB/s (algorithmic bytes / event-timed launch)", "unit": "GB/s",
-                      "workload": wl.name, "lattice": f"{wl.ns}^3x{wl.nt}", "peak": hbm,
+                      "workload": wl.name, "lattice": f"{wl.ns}^3x{wl.nt}", "peak": hbm, "kernel_version": HOP_KERNEL_VERSION,
                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                       "rows": rows}), flush=True)
 

@@ -368,6 +368,142 @@ int correlate(laph_ctx *ctx, const laph_lattice *lat, const laph_corr_spec *spec
               const void *const *coef, const uint8_t *const *noise, void *corr, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Momentum and same-time pieces of the meson correlators (Sec. III: the phase
+ * e^{-ip.x} of Eq. (mesonfunc) without displacement; the second term of
+ * Eq. (mesoncorr), the isoscalar "smt" diagram of Sec. V).  Momenta are integer
+ * triples (px, py, pz), p = 2 pi (px, py, pz) / ns; x is the site's spatial
+ * position (x fastest).  All arithmetic FP64; arrays host or device.
+ *
+ * laph_mom_overlaps: Phi_p(t)[n][n'] = sum_{x,c} conj(V(t,n,x,c)) e^{-ip.x} V(t,n',x,c)
+ *   for nmom momenta (mom: host [nmom][3] ints); phi [nmom][nt][nv][nv] c128.
+ *   Phi_0 is the identity for orthonormal eigenvectors.
+ *
+ * correlate_mom: the meson channels of correlate() (pion, rho, scalar) at momentum p:
+ *   both meson functions of Eq. (mesoncorr) take e^{-ip.x}, which in LapH
+ *   coordinates puts phi = Phi_p [nt][nv][nv] between the two lines:
+ *   M^[b1 b2](a, b; t) = sum conj(a^[b1](t,alpha,n)) W_{alpha beta} Phi_p(t)[n][n'] b^[b2](t,beta,n').
+ *   spec, coef, noise, corr as in correlate() with two lines.
+ *
+ * laph_meson_loops: same-time line of one noise closed on every slice,
+ *   loops[c][t] = sum_b M^[bb](varrho, varphi; t)           (reverse = 0)
+ *   loops[c][t] = sum_b M^[bb](varphi, varrho; t)           (reverse = 1)
+ *   with the channel's c = gamma_4 Gamma (no gamma_5 swap), one row per component
+ *   (nc = 3 for the rho, else 1), phi = Phi_p or NULL for p = 0.  coef
+ *   [nb][nt][4][nv] and noise [nt][4][nv] of one line whose projectors
+ *   (spec->b_list) cover every slice to be used (time interlacing, all solved).
+ *   loops [nc][nt] c128.
+ *
+ * correlate_disconnected: corr[dt] = (1/nc) sum_c loops1[c][(t0+dt) mod nt]
+ *   conj(loops2[c][t0]) - vev, with loops1 forward and loops2 reversed lines of
+ *   two independent noises.  For the two degenerate light flavours the isoscalar
+ *   correlator is corr_connected + 2 corr_disconnected (flavour weights of
+ *   (u-bar Gamma u + d-bar Gamma d)/sqrt 2); vev = <L_1> conj(<L_2>) for the scalar.
+ * ------------------------------------------------------------------------ */
+int laph_mom_overlaps(laph_ctx *ctx, const laph_lattice *lat, const void *evecs, int nv, int nmom, const int *mom,
+                      void *phi, void *stream);
+int correlate_mom(laph_ctx *ctx, const laph_lattice *lat, const laph_corr_spec *spec, const void *const *coef,
+                  const uint8_t *const *noise, const void *phi, void *corr, void *stream);
+int laph_meson_loops(laph_ctx *ctx, const laph_lattice *lat, const laph_corr_spec *spec, const void *coef,
+                     const uint8_t *noise, const void *phi, int reverse, void *loops, void *stream);
+int correlate_disconnected(laph_ctx *ctx, const laph_lattice *lat, int t0, int nc, const void *loops1,
+                           const void *loops2, double vev_re, double vev_im, void *corr, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Displaced overlaps (Sec. II: the quark line D^(j) S Omega^{-1} S D^(k)dag of
+ * Eq. (quarkdef); Sec. III: the phase e^{-ip.(x + (d_j + d_k)/2)} of Eq. (mesonfunc)):
+ *   (D psi)(x) = U_{s1}(x) U_{s2}(x+s1) ... psi(x + s1 + ... + sL), a step -mu
+ *   through U_mu(y - mu)^dag, steps s = +-1, +-2, +-3 (x, y, z), at most 64;
+ *   Phi_{p,jk}(t)[n][n'] = e^{-ip.(d_j+d_k)/2} sum_{x,c} conj((D^(j) V_n)(x,c)) e^{-ip.x} (D^(k) V_n')(x,c)
+ * for qbar displaced along path_bar (j) and q along path (k); d the net displacements.
+ *   links3d [V][4][3][3] c128 (the Laplacian's smeared links), evecs as laph_eigvecs,
+ *   mom host int[3], paths host int arrays (empty: no displacement), phi [nt][nv][nv] c128.
+ * correlate_mom with phi = Phi_{p,jk} gives the connected correlator of the displaced
+ * elemental (c, p, j, k) (the sink and the source function take the same (c, p, j, k)).
+ * ------------------------------------------------------------------------ */
+int laph_displaced_overlaps(laph_ctx *ctx, const laph_lattice *lat, const void *links3d, const void *evecs, int nv,
+                            const int *mom, int len_bar, const int *path_bar, int len, const int *path, void *phi,
+                            void *stream);
+
+/* ------------------------------------------------------------------------
+ * Two-pion correlators of isospin I = 0, 1, 2 (Sec. III two-meson diagrams,
+ * Sec. V two-pion operators): the state |I, I3> of a pion of momentum p and
+ * one of -p (pi+ = ubar d, pi0 = (dbar d - ubar u)/sqrt 2, pi- = -dbar u,
+ * coupled by the Clebsch-Gordan coefficients of 1 x 1; c = gamma_4 gamma_5),
+ * its source partner at t0, and every Wick contraction of the four bilinears
+ * (direct, crossed, box and vacuum diagrams), each propagator a line estimate:
+ *   - antiquark end at the source: forward line k, sum_b phi^[b] rho^[b]dag;
+ *   - sink to source: forward line k through gamma_5 Hermiticity,
+ *     G' (sum_b phi^[b] rho^[b]dag)^dag G', G' = gamma_4 gamma_5;
+ *   - sink to sink: same-time line k.
+ * A term's propagators take forward lines 0, 1, 2, 3 and same-time lines 0, 1
+ * in the order its cycles are visited (cycles started from the lowest unvisited
+ * bilinear, sink bilinears 0 (p) and 1 (-p), source bilinears 2 and 3).  At
+ * t_F = t0 the sink bilinears keep the sink rules.
+ *   coef_fwd[4] [nb_fwd][nt][4][nv], noise_fwd[4] [nt][4][nv]: lines sourced at
+ *     t0 (b_fwd: the projectors whose time support holds t0);
+ *   coef_smt[2] [nb_smt][nt][4][nv], noise_smt[2]: same-time lines, every
+ *     projector of dil_smt solved, each slice covered by equally many
+ *     projectors; needed (non-null) only where a diagram uses them (I < 2 or
+ *     I3 < I);
+ *   phi_p, phi_mp [nt][nv][nv] c128: Phi_p and Phi_-p (laph_mom_overlaps), or
+ *     both NULL for p = 0;
+ *   corr [nt] c128, corr[dt] = <pipi(t0 + dt) pipi-bar(t0)> (no vacuum
+ *     subtraction).  Scratch about (nt nb^2) complex doubles per distinct
+ *     meson function, nb the larger of nb_fwd and the projectors per slice.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int iso, iso3;            /* total isospin I and I3 (0 <= I3 <= I <= 2)         */
+    int t0;
+    int nv;
+    laph_dilution dil_fwd;    /* forward lines                                      */
+    int nb_fwd;
+    const int *b_fwd;         /* [nb_fwd] host                                      */
+    laph_dilution dil_smt;    /* same-time lines                                    */
+    int nb_smt;
+    const int *b_smt;         /* [nb_smt] host (NULL when nb_smt = 0)               */
+} laph_pipi_spec;
+
+int correlate_pipi(laph_ctx *ctx, const laph_lattice *lat, const laph_pipi_spec *spec, const void *const *coef_fwd,
+                   const uint8_t *const *noise_fwd, const void *const *coef_smt, const uint8_t *const *noise_smt,
+                   const void *phi_p, const void *phi_mp, void *corr, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Baryons (Sec. III: three-quark elemental operators, Eq. (baryonfunc) and
+ * Eq. (baryoncorr)).  All arithmetic FP64; arrays host or device.
+ *
+ * laph_baryon_tensor: T_p(t)[n1][n2][n3] = sum_x e^{-ip.x} eps_abc
+ *   V(t,n1,x,a) V(t,n2,x,b) V(t,n3,x,c), antisymmetric in (n1, n2, n3);
+ *   evecs as laph_eigvecs, mom host int[3], T [nt][nv][nv][nv] c128, nv <= 512.
+ *
+ * correlate_baryon: the correlator of Eq. (baryoncorr) for one source time,
+ *   corr[dt] = sum_{b1 b2 b3} B^[b1 b2 b3](phi_1, phi_2, phi_3; t0 + dt)
+ *              conj( sum_pi sgn(pi) B^[b_pi0 b_pi1 b_pi2](rho_pi0, rho_pi1, rho_pi2; t0) ),
+ *   B^[b1 b2 b3](f1, f2, f3; t) = c_{alpha beta gamma} sum_{n1 n2 n3} T_p(t)[n1][n2][n3]
+ *                                 f1^[b1](t,alpha,n1) f2^[b2](t,beta,n2) f3^[b3](t,gamma,n3)
+ *   (c_snk at the sink, c_src at the source); pi runs over the orderings of the
+ *   three lines for which sink quark pi(s) has the flavour of source slot s.
+ *   coef[k] = [nb][nt][4][nv] and noise[k] = [nt][4][nv] of line k (three lines,
+ *   one noise each, the same nb, b_list and dilution), T from laph_baryon_tensor.
+ *   corr [nt] c128.  Scratch about nt nv nb^2 (16 + nv/4) + nt nb^3 complex doubles.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int t0;                   /* source time                                        */
+    int nv;
+    laph_dilution dil;        /* dilution of every line                             */
+    int nb;                   /* projectors per line (<= 1024)                      */
+    const int *b_list;        /* [nb] flat projector indices (host)                 */
+    const double *c_snk;      /* [4][4][4] complex, re/im interleaved (host)        */
+    const double *c_src;      /* [4][4][4] complex, re/im interleaved (host)        */
+    int flav_snk[3];          /* flavour labels of the sink quarks (A, B, C)        */
+    int flav_src[3];          /* flavour labels of the source slots                 */
+} laph_baryon_spec;
+
+int laph_baryon_tensor(laph_ctx *ctx, const laph_lattice *lat, const void *evecs, int nv, const int *mom, void *T,
+                       void *stream);
+int correlate_baryon(laph_ctx *ctx, const laph_lattice *lat, const laph_baryon_spec *spec, const void *const *coef,
+                     const uint8_t *const *noise, const void *T, void *corr, void *stream);
+
+/* ------------------------------------------------------------------------
  * correlate_noalloc: the same correlators as correlate(), for callers that
  * cannot allocate GPU memory (no counterpart in the paper; it exists for
  * callers such as code running inside a caller-owned memory pool or arena,

@@ -379,6 +379,90 @@ void mrhs_copy_scaled_bf16(long nrows, int nr, const double *scale, const c64 *x
     prof_end("blas_convert", s, 0.0, 0.0);
 }
 
+// ------------------------------------------------------------------ generated shadow vector
+// code[cb][r] = packed rhat_quant of the 12 components of site cb, right-hand side r
+__global__ void rhat_pack_kernel(long nsite, int nr, const c32 *__restrict__ r, uint32_t *__restrict__ code) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nsite * nr) return;
+    const long cb = idx / nr, k = idx - cb * nr;
+    uint32_t w = 0;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const c32 v = r[(cb * 12 + c) * nr + k];
+        w |= rhat_quant(v.re, v.im) << (2 * c);
+    }
+    code[idx] = w;
+}
+
+struct RhatDots {
+    const c32 *v;
+    const uint32_t *code;
+    int nr;
+    using Acc = c32;
+    __device__ void operator()(long i, int, Acc *acc) const {
+        const c32 w = v[i];
+        acc[0] += rhat_conj_mul(rhat_code_at(code, i, nr), w);
+        acc[1] += cmul_conj(w, w);
+    }
+    __device__ void two(long i, long j, int k, Acc *acc) const {
+        (*this)(i, k, acc);
+        (*this)(j, k, acc);
+    }
+};
+void mrhs_rhat_dots(laph_ctx *ctx, const RedPlan &pl, long nrows, const c32 *v, const uint32_t *code, c64 *red,
+                    cudaStream_t s) {
+    run_reduce<2>(ctx, pl, nrows, RhatDots{v, code, pl.nr}, red, s, nullptr,
+                  (double)nrows * pl.nr * (sizeof(c32) + 4.0 / 12.0));
+}
+void mrhs_rhat_init(laph_ctx *ctx, const RedPlan &pl, long nrows, const c32 *r, uint32_t *code, c64 *red,
+                    cudaStream_t s) {
+    const long nsite = nrows / 12;
+    rhat_pack_kernel<<<grid_for(nsite * pl.nr, 256), 256, 0, s>>>(nsite, pl.nr, r, code);
+    LAPH_LAUNCH_CHECK();
+    mrhs_rhat_dots(ctx, pl, nrows, r, code, red, s);
+}
+
+struct XRGenBody {
+    BicgScalars sc;
+    c32 *x;
+    const c32 *p, *sv, *t;
+    c32 *r;
+    const uint32_t *code;
+    int nr;
+    using Acc = c32;
+    __device__ void operator()(long i, int k, Acc *acc) const {
+        const c32 a = cvt<float>(sc.alpha[k]), w = cvt<float>(sc.omega[k]);
+        const c32 si = sv[i];
+        x[i] = x[i] + a * p[i] + w * si;
+        const c32 rn = si - w * t[i];
+        r[i] = rn;
+        acc[0] += rhat_conj_mul(rhat_code_at(code, i, nr), rn);
+        acc[1] += cmul_conj(rn, rn);
+    }
+    __device__ void two(long i, long j, int k, Acc *acc) const {
+        const c32 a = cvt<float>(sc.alpha[k]), w = cvt<float>(sc.omega[k]);
+        const c32 xi = x[i], pi = p[i], si = sv[i], ti = t[i];
+        const c32 xj = x[j], pj = p[j], sj = sv[j], tj = t[j];
+        const uint32_t qi = rhat_code_at(code, i, nr), qj = rhat_code_at(code, j, nr);
+        const c32 ri = si - w * ti, rj = sj - w * tj;
+        x[i] = xi + a * pi + w * si;
+        x[j] = xj + a * pj + w * sj;
+        r[i] = ri;
+        r[j] = rj;
+        acc[0] += rhat_conj_mul(qi, ri);
+        acc[1] += cmul_conj(ri, ri);
+        acc[0] += rhat_conj_mul(qj, rj);
+        acc[1] += cmul_conj(rj, rj);
+    }
+};
+void bicg_xr_update_reduce_gen(laph_ctx *ctx, const RedPlan &pl, long nrows, const BicgScalars &sc, c32 *x,
+                               const c32 *p, const c32 *sv, const c32 *t, c32 *r, const uint32_t *code, c64 *red,
+                               cudaStream_t s) {
+    // read x, p, s, t and the codes; write x, r
+    run_reduce<2>(ctx, pl, nrows, XRGenBody{sc, x, p, sv, t, r, code, pl.nr}, red, s, nullptr,
+                  (6.0 * sizeof(c32) + 4.0 / 12.0) * nrows * pl.nr);
+}
+
 __device__ __forceinline__ c64 cdiv(c64 a, c64 b) {
     double d = norm2(b);
     return c64{(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
@@ -410,6 +494,29 @@ __global__ void init_scalars_kernel(int nr, BicgScalars sc, const c64 *red_rr, d
 }
 void bicg_init_scalars(int nr, const BicgScalars &sc, const c64 *red_rr, double rel_tol, cudaStream_t s) {
     init_scalars_kernel<<<grid_for(nr, 64), 64, 0, s>>>(nr, sc, red_rr, rel_tol);
+    LAPH_LAUNCH_CHECK();
+}
+
+// coded shadow vector: rho = <rhat, r0>, rr = <r0, r0>
+__global__ void init_scalars_gen_kernel(int nr, BicgScalars sc, const c64 *red, double rel_tol) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr) return;
+    const c64 rho = red[k];
+    const double rr = red[nr + k].re;
+    sc.rho[k] = rho;
+    sc.alpha[k] = c64{1.0, 0.0};
+    sc.omega[k] = c64{1.0, 0.0};
+    sc.beta[k] = rho;   // (rho / rho_old)(alpha / omega) with rho_old = 1: p = r first
+    sc.rr[k] = rr;
+    sc.rr_stop[k] = rel_tol * rel_tol * rr;
+    sc.iters[k] = 0;
+    const bool run = rr > 0.0 && isfinite(rr) && norm2(rho) > 0.0;
+    sc.active[k] = run ? 1 : 0;
+    sc.status[k] = run ? 0 : (rr > 0.0 ? 2 : 1);
+    if (!run) deactivate(sc, k, sc.status[k]);
+}
+void bicg_init_scalars_gen(int nr, const BicgScalars &sc, const c64 *red, double rel_tol, cudaStream_t s) {
+    init_scalars_gen_kernel<<<grid_for(nr, 64), 64, 0, s>>>(nr, sc, red, rel_tol);
     LAPH_LAUNCH_CHECK();
 }
 

@@ -13,59 +13,9 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gamma_host.cuh"
 
 namespace laph {
-
-std::vector<uint8_t> dilution_masks(const laph_dilution &d, int nt, int nv, const int *b_list, int nb);
-
-// ----------------------------------------------------------------- Dirac matrices (host)
-struct Mat4 {
-    c64 m[4][4];
-};
-
-static Mat4 mat_zero() {
-    Mat4 r;
-    for (auto &row : r.m)
-        for (auto &v : row) v = {0, 0};
-    return r;
-}
-static Mat4 mat_mul(const Mat4 &a, const Mat4 &b) {
-    Mat4 r = mat_zero();
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j)
-            for (int k = 0; k < 4; ++k) r.m[i][j] += a.m[i][k] * b.m[k][j];
-    return r;
-}
-static Mat4 mat_dag(const Mat4 &a) {
-    Mat4 r;
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) r.m[i][j] = conj(a.m[j][i]);
-    return r;
-}
-static Mat4 mat_scale(double s, const Mat4 &a) {
-    Mat4 r;
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) r.m[i][j] = s * a.m[i][j];
-    return r;
-}
-// chiral basis: gamma_mu = [[0, G], [G^dag, 0]], G_k = -i sigma_k, G_4 = 1
-static Mat4 gamma_mat(int mu) {
-    const c64 O{0, 0}, P{1, 0}, M1{-1, 0}, I{0, 1}, Mi{0, -1};
-    c64 G[4][2][2] = {{{O, Mi}, {Mi, O}}, {{O, M1}, {P, O}}, {{Mi, O}, {O, I}}, {{P, O}, {O, P}}};
-    Mat4 r = mat_zero();
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j) {
-            r.m[i][2 + j] = G[mu][i][j];
-            r.m[2 + i][j] = conj(G[mu][j][i]);
-        }
-    return r;
-}
-static Mat4 gamma5() { return mat_mul(mat_mul(gamma_mat(0), gamma_mat(1)), mat_mul(gamma_mat(2), gamma_mat(3))); }
-static Mat4 ident4() {
-    Mat4 r = mat_zero();
-    for (int i = 0; i < 4; ++i) r.m[i][i] = {1, 0};
-    return r;
-}
 
 // ----------------------------------------------------------------- kernels
 // rho_src[b][alpha][n] = mask_b(t0,alpha,n) i^code(t0,alpha,n)
@@ -82,10 +32,6 @@ __global__ void rho_at_t0_kernel(int nt, int nv, int nb, int t0, const uint8_t *
     }
     out[idx] = v;
 }
-
-struct W4 {
-    c64 w[4][4];
-};
 
 // M[t][b1][b2] = sum_n sum_{a,b} conj(A[b1][tA][a][n]) W[a][b] B[b2][tB][b][n]
 // A, B: [nb][ntA][4][nv]; the slice used is t (or 0 when the operand has a single slice).
@@ -159,13 +105,6 @@ __global__ void pipi_x_kernel(int nt, int nb, int t0, const c64 *P, const c64 *S
         __syncthreads();
     }
     if (threadIdx.x == 0) corr[dt] = cpi12[dt] * cpi34[dt] - sm[0];
-}
-
-static W4 to_w4(const Mat4 &m) {
-    W4 w;
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) w.w[i][j] = m.m[i][j];
-    return w;
 }
 
 struct LineDev {

@@ -70,6 +70,11 @@ void hop_f32(const DiracOp &op, int p, HopMode mode, cpx<float> *out, const cpx<
 bool hop_f32_xpay_dots(laph_ctx *ctx, const DiracOp &op, int p, cpx<float> *out, const cpx<float> *in,
                        const cpx<float> *z, int nr, cpx<double> *red, cudaStream_t s);
 
+// The same with <rhat, out> (the coded shadow vector of blas.cuh, rcode [Vh][nr] packed words) fused
+// instead: red[0][r] = <rhat, out>.
+bool hop_f32_xpay_rdot(laph_ctx *ctx, const DiracOp &op, int p, cpx<float> *out, const cpx<float> *in,
+                       const cpx<float> *z, int nr, const uint32_t *rcode, cpx<double> *red, cudaStream_t s);
+
 // BF16-stored spinors ([cb][12][nr] bf162: one complex per element), FP32 links and clover inverse, FP32
 // arithmetic: the copy-engine-fed kernel of hop_f32 reading and writing BF16 tiles.  nr must be 32, 64,
 // 128 or 256.  The xpay form with the fused <out, z>, <out, out> returns false where unavailable.

@@ -235,12 +235,12 @@ __device__ int g_hop3_timeout;   // set when a copy wait gives up (or the ring i
 // DOTS (xpay mode, nr = 32 RPT): the epilogue also accumulates, per right-hand side, the inner
 // products <out, z> and <out, out> of the warp's sites in FP32 and writes them as the warp's
 // partial sums partial[warp][k][r] (k = 0, 1; FP64) for a fixed-order final sum.
-template <int MODE, int NS, int RPT, bool DOTS = false, typename E = float2, int HPJ = 1>
+template <int MODE, int NS, int RPT, int DOTS = 0, typename E = float2, int HPJ = 1>
 __global__ void __launch_bounds__(HOP3_WARPS * 32, 4)
     hop3_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_z,
                 const int *__restrict__ nbr, const int *__restrict__ order, const float4 *__restrict__ L,
                 const float *__restrict__ C, int Vh, int p, float hws, float hwt, E *__restrict__ out, int nr, int gshift,
-                int nunits, c64 *__restrict__ partial) {
+                int nunits, c64 *__restrict__ partial, const uint32_t *__restrict__ rcode) {
     extern __shared__ __align__(128) unsigned char sm3[];
     constexpr int HOP3_SPIN = Hop3Geo<RPT, E, HPJ>::SPIN, HOP3_SLOT = Hop3Geo<RPT, E, HPJ>::SLOT;
     constexpr int NJ = Hop3Geo<RPT, E, HPJ>::JOBS;
@@ -347,6 +347,10 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, 4)
     bool ok = true;
     for (int k = 0, q = gw; k < nu && ok; ++k, q += gstride) {
         const int cb = __ldg(order + (q >> gshift)), h = q & gmask;
+        // packed shadow-vector codes, fetched before the hops so that their latency is hidden
+        uint32_t rw[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) rw[q] = DOTS == 2 ? __ldg(rcode + (long)cb * nr + 32 * q + lane) : 0u;
         float2 acc[RPT][12];
 #pragma unroll
         for (int q = 0; q < RPT; ++q)
@@ -426,11 +430,15 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, 4)
                     for (int c = 0; c < 12; ++c) {
                         const float2 zc = to_f2(zs[c * 32 * RPT]);
                         res[q][c] = sub2(zc, res[q][c]);
-                        if (DOTS) {   // conj(t) z and |t|^2
+                        if (DOTS == 1) {   // conj(t) z and |t|^2
                             const float2 t = res[q][c];
                             dts[q].x = fmaf(t.x, zc.x, fmaf(t.y, zc.y, dts[q].x));
                             dts[q].y = fmaf(t.x, zc.y, fmaf(-t.y, zc.x, dts[q].y));
                             dtt[q] = fmaf(t.x, t.x, fmaf(t.y, t.y, dtt[q]));
+                        } else if (DOTS == 2) {   // conj(rhat) t with the coded shadow vector (nr = 32 RPT)
+                            const c32 v = rhat_conj_mul((rw[q] >> (2 * c)) & 3u, c32{res[q][c].x, res[q][c].y});
+                            dts[q].x += v.re;
+                            dts[q].y += v.im;
                         }
                     }
                 }
@@ -444,7 +452,7 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, 4)
             for (int c = 0; c < 12; ++c) dst[(long)c * nr] = from_f2<E>(res[q][c]);
         }
     }
-    if (DOTS) {   // every warp writes, zeros where it had no units
+    if (DOTS != 0) {   // every warp writes, zeros where it had no units
         const int gwarp = blockIdx.x * HOP3_WARPS + warp;
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
@@ -492,9 +500,10 @@ static CUtensorMap spinor_map(const E *base, long Vh, int nr, int rpt) {
     return m;
 }
 
-template <int MODE, int NS, int RPT, bool DOTS = false, typename E = float2>
+template <int MODE, int NS, int RPT, int DOTS = 0, typename E = float2>
 static long launch_hop3(const DiracOp &op, int p, float hws, float hwt, E *out, const E *in,
-                        const E *z, int nr, cudaStream_t s, laph_ctx *ctx = nullptr, c64 *red = nullptr) {
+                        const E *z, int nr, cudaStream_t s, laph_ctx *ctx = nullptr, c64 *red = nullptr,
+                        const uint32_t *rcode = nullptr) {
     // one RHS per lane: two hops per job (the slot still leaves room for four blocks per SM)
     constexpr int HPJ = RPT == 1 ? 2 : 1;
     constexpr size_t smem = (size_t)HOP3_WARPS * NS * (Hop3Geo<RPT, E, HPJ>::SLOT + 8 + 8);
@@ -520,12 +529,11 @@ static long launch_hop3(const DiracOp &op, int p, float hws, float hwt, E *out, 
     const long cap = (long)bpsm[dev] * nsm[dev];
     if (grid > cap) grid = cap;
     c64 *partial = nullptr;
-    if (DOTS) partial = (c64 *)ws_get(ctx, "hop3:dots", sizeof(c64) * 2 * nr * grid * HOP3_WARPS);
+    if (DOTS != 0) partial = (c64 *)ws_get(ctx, "hop3:dots", sizeof(c64) * 2 * nr * grid * HOP3_WARPS);
     hop3_kernel<MODE, NS, RPT, DOTS, E, HPJ><<<(unsigned)grid, HOP3_WARPS * 32, smem, s>>>(
         tin, tz, op.nbr, op.order, op.L32w, MODE == HOP_APPLY ? op.C32wA : op.C32w, (int)op.g.Vh, p, hws, hwt, out, nr,
-        gshift,
-        (int)nunits, partial);
-    if (DOTS) {
+        gshift, (int)nunits, partial, rcode);
+    if (DOTS != 0) {
         LAPH_LAUNCH_CHECK();
         red_final_sum(partial, (int)(grid * HOP3_WARPS), 2, nr, red, s);
     }
@@ -627,13 +635,32 @@ bool hop_f32_xpay_dots(laph_ctx *ctx, const DiracOp &op, int p, c32 *out, const 
     float hws = (float)op.hw[0], hwt = (float)op.hw[3];
     prof_begin("dslash_fp32", s);
     if (rpt == 2)
-        launch_hop3<HOP_CLOVINV_XPAY, 2, 2, true>(op, p, hws, hwt, (float2 *)out, (const float2 *)in,
+        launch_hop3<HOP_CLOVINV_XPAY, 2, 2, 1>(op, p, hws, hwt, (float2 *)out, (const float2 *)in,
                                                   (const float2 *)z, nr, s, ctx, red);
     else
-        launch_hop3<HOP_CLOVINV_XPAY, 2, 1, true>(op, p, hws, hwt, (float2 *)out, (const float2 *)in,
+        launch_hop3<HOP_CLOVINV_XPAY, 2, 1, 1>(op, p, hws, hwt, (float2 *)out, (const float2 *)in,
                                                   (const float2 *)z, nr, s, ctx, red);
     LAPH_LAUNCH_CHECK();
     prof_end("dslash_fp32", s, hop_bytes(op, HOP_CLOVINV_XPAY, nr, sizeof(float)), hop_flops(op, nr));
+    return true;
+}
+
+// The xpay hop out = z - A_pp^{-1} D in with <rhat, out> of every right-hand side fused into its
+// epilogue (rhat the coded shadow vector of blas.cuh, rcode[cb][r] packed words): red[0][r] = <rhat, out>,
+// red[1][r] = 0.
+bool hop_f32_xpay_rdot(laph_ctx *ctx, const DiracOp &op, int p, c32 *out, const c32 *in, const c32 *z, int nr,
+                       const uint32_t *rcode, c64 *red, cudaStream_t s) {
+    // one right-hand side per lane only: with two the fused epilogue spills registers
+    const bool aligned = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(z) |
+                           reinterpret_cast<uintptr_t>(op.L32w) | reinterpret_cast<uintptr_t>(op.C32w)) & 15) == 0;
+    if (!aligned || hop3_stages() != 2 || nr != 32) return false;
+    float hws = (float)op.hw[0], hwt = (float)op.hw[3];
+    prof_begin("dslash_fp32", s);
+    launch_hop3<HOP_CLOVINV_XPAY, 2, 1, 2>(op, p, hws, hwt, (float2 *)out, (const float2 *)in, (const float2 *)z, nr,
+                                           s, ctx, red, rcode);
+    LAPH_LAUNCH_CHECK();
+    prof_end("dslash_fp32", s, hop_bytes(op, HOP_CLOVINV_XPAY, nr, sizeof(float)) + (double)op.g.Vh * 4 * nr,
+             hop_flops(op, nr));
     return true;
 }
 
@@ -664,16 +691,16 @@ void hop_bf16(const DiracOp &op, int p, HopMode mode, __nv_bfloat162 *out, const
     prof_begin("dslash_bf16", s);
     const bool two = hop3_rpt_max() == 2 && nr % 64 == 0;
     if (mode == HOP_APPLY)
-        two ? (void)launch_hop3<HOP_APPLY, 2, 2, false>(op, p, hws, hwt, out, in, z, nr, s)
-            : (void)launch_hop3<HOP_APPLY, 2, 1, false>(op, p, hws, hwt, out, in, z, nr, s);
+        two ? (void)launch_hop3<HOP_APPLY, 2, 2, 0>(op, p, hws, hwt, out, in, z, nr, s)
+            : (void)launch_hop3<HOP_APPLY, 2, 1, 0>(op, p, hws, hwt, out, in, z, nr, s);
     else if (mode == HOP_CLOVINV)
-        two ? (void)launch_hop3<HOP_CLOVINV, 2, 2, false>(op, p, hws, hwt, out, in, (const __nv_bfloat162 *)nullptr,
+        two ? (void)launch_hop3<HOP_CLOVINV, 2, 2, 0>(op, p, hws, hwt, out, in, (const __nv_bfloat162 *)nullptr,
                                                           nr, s)
-            : (void)launch_hop3<HOP_CLOVINV, 2, 1, false>(op, p, hws, hwt, out, in, (const __nv_bfloat162 *)nullptr,
+            : (void)launch_hop3<HOP_CLOVINV, 2, 1, 0>(op, p, hws, hwt, out, in, (const __nv_bfloat162 *)nullptr,
                                                           nr, s);
     else
-        two ? (void)launch_hop3<HOP_CLOVINV_XPAY, 2, 2, false>(op, p, hws, hwt, out, in, z, nr, s)
-            : (void)launch_hop3<HOP_CLOVINV_XPAY, 2, 1, false>(op, p, hws, hwt, out, in, z, nr, s);
+        two ? (void)launch_hop3<HOP_CLOVINV_XPAY, 2, 2, 0>(op, p, hws, hwt, out, in, z, nr, s)
+            : (void)launch_hop3<HOP_CLOVINV_XPAY, 2, 1, 0>(op, p, hws, hwt, out, in, z, nr, s);
     LAPH_LAUNCH_CHECK();
     prof_end("dslash_bf16", s, hop_bytes_bf16(op, mode, nr), hop_flops(op, nr));
 }
@@ -685,9 +712,9 @@ bool hop_bf16_xpay_dots(laph_ctx *ctx, const DiracOp &op, int p, __nv_bfloat162 
     const float hws = (float)op.hw[0], hwt = (float)op.hw[3];
     prof_begin("dslash_bf16", s);
     if (rpt == 2)
-        launch_hop3<HOP_CLOVINV_XPAY, 2, 2, true>(op, p, hws, hwt, out, in, z, nr, s, ctx, red);
+        launch_hop3<HOP_CLOVINV_XPAY, 2, 2, 1>(op, p, hws, hwt, out, in, z, nr, s, ctx, red);
     else
-        launch_hop3<HOP_CLOVINV_XPAY, 2, 1, true>(op, p, hws, hwt, out, in, z, nr, s, ctx, red);
+        launch_hop3<HOP_CLOVINV_XPAY, 2, 1, 1>(op, p, hws, hwt, out, in, z, nr, s, ctx, red);
     LAPH_LAUNCH_CHECK();
     prof_end("dslash_bf16", s, hop_bytes_bf16(op, HOP_CLOVINV_XPAY, nr), hop_flops(op, nr));
     return true;

@@ -55,8 +55,12 @@ static InnerStats bicgstab_schur(laph_ctx *ctx, const DiracOp &op, int nr, const
     long nrows = g.Vh * 12;
     size_t vb = sizeof(cpx<T>) * nrows * nr;
     auto V = [&](const char *n) { return (cpx<T> *)ws_get(ctx, tag + n, vb); };
-    cpx<T> *r = V(":r"), *rh = V(":rh"), *p = V(":p"), *v = V(":v"), *sv = V(":s"), *t = V(":t");
+    // FP32: the shadow vector is the rounded phase of r0 stored as packed 2-bit codes (blas.cuh),
+    // and <rhat, v> comes out of the stencil's epilogue; FP64 (the plain solver): rhat = r0, stored
+    constexpr bool gen = std::is_same<T, float>::value;
+    cpx<T> *r = V(":r"), *rh = gen ? nullptr : V(":rh"), *p = V(":p"), *v = V(":v"), *sv = V(":s"), *t = V(":t");
     cpx<T> *tmp = V(":tmp");
+    uint32_t *rc = gen ? (uint32_t *)ws_get(ctx, tag + ":rc", sizeof(uint32_t) * (size_t)(nrows / 12) * nr) : nullptr;
     char *scb = (char *)ws_get(ctx, tag + ":sc", (sizeof(c64) * 4 + sizeof(double) * 2 + sizeof(int) * 3) * nr + 256);
     BicgScalars sc;
     sc.rho = (c64 *)scb;
@@ -75,21 +79,37 @@ static InnerStats bicgstab_schur(laph_ctx *ctx, const DiracOp &op, int nr, const
     LAPH_CUDA(cudaMemsetAsync(p, 0, vb, s));
     LAPH_CUDA(cudaMemsetAsync(v, 0, vb, s));
     LAPH_CUDA(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, s));
-    LAPH_CUDA(cudaMemcpyAsync(rh, b, vb, cudaMemcpyDeviceToDevice, s));
-    mrhs_dots<T>(ctx, pl, nrows, 1, r, r, nullptr, nullptr, nullptr, nullptr, red, s);
-    bicg_init_scalars(nr, sc, red, rel_tol, s);
+    if constexpr (gen) {
+        mrhs_rhat_init(ctx, pl, nrows, (const c32 *)r, rc, red, s);
+        bicg_init_scalars_gen(nr, sc, red, rel_tol, s);
+    } else {
+        LAPH_CUDA(cudaMemcpyAsync(rh, b, vb, cudaMemcpyDeviceToDevice, s));
+        mrhs_dots<T>(ctx, pl, nrows, 1, r, r, nullptr, nullptr, nullptr, nullptr, red, s);
+        bicg_init_scalars(nr, sc, red, rel_tol, s);
+    }
 
     int *h_flags = (int *)pinned_get(ctx, sizeof(int) * 3 * nr);
     if (check_every < 1) check_every = 5;
     for (int it = 0; it < maxiter; ++it) {
         bicg_p_update<T>(nrows, nr, sc, r, p, v, s);
-        schur_apply<T>(op, nr, p, v, tmp, s);
-        mrhs_dots<T>(ctx, pl, nrows, 1, rh, v, nullptr, nullptr, nullptr, nullptr, red, s);
+        if constexpr (gen) {   // v = M p with <rhat, v>
+            hop<T>(op, 1, HOP_CLOVINV, tmp, p, nullptr, nullptr, nr, s);
+            if (!hop_f32_xpay_rdot(ctx, op, 0, v, tmp, p, nr, rc, red, s)) {
+                hop<T>(op, 0, HOP_CLOVINV_XPAY, v, tmp, p, nullptr, nr, s);
+                mrhs_rhat_dots(ctx, pl, nrows, v, rc, red, s);
+            }
+        } else {
+            schur_apply<T>(op, nr, p, v, tmp, s);
+            mrhs_dots<T>(ctx, pl, nrows, 1, rh, v, nullptr, nullptr, nullptr, nullptr, red, s);
+        }
         bicg_alpha(nr, sc, red, s);
         bicg_s_update<T>(nrows, nr, sc, r, v, sv, s);
         schur_apply_tdots<T>(ctx, pl, nrows, op, nr, sv, t, tmp, red, s);
         bicg_omega(nr, sc, red, s);
-        bicg_xr_update_reduce<T>(ctx, pl, nrows, sc, x, p, sv, t, r, rh, red, s);
+        if constexpr (gen)
+            bicg_xr_update_reduce_gen(ctx, pl, nrows, sc, x, p, sv, t, r, rc, red, s);
+        else
+            bicg_xr_update_reduce<T>(ctx, pl, nrows, sc, x, p, sv, t, r, rh, red, s);
         bicg_rho(nr, sc, red, s);
         if ((it + 1) % check_every == 0 || it + 1 == maxiter) {
             LAPH_CUDA(cudaMemcpyAsync(h_flags, sc.active, sizeof(int) * nr, cudaMemcpyDeviceToHost, s));

@@ -74,6 +74,19 @@ class CorrSpec(ctypes.Structure):
                 ("nb", ctypes.c_int), ("b_list", ctypes.POINTER(ctypes.c_int))]
 
 
+class PipiSpec(ctypes.Structure):
+    _fields_ = [("iso", ctypes.c_int), ("iso3", ctypes.c_int), ("t0", ctypes.c_int), ("nv", ctypes.c_int),
+                ("dil_fwd", Dilution), ("nb_fwd", ctypes.c_int), ("b_fwd", ctypes.POINTER(ctypes.c_int)),
+                ("dil_smt", Dilution), ("nb_smt", ctypes.c_int), ("b_smt", ctypes.POINTER(ctypes.c_int))]
+
+
+class BaryonSpec(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_int), ("nv", ctypes.c_int), ("dil", Dilution), ("nb", ctypes.c_int),
+                ("b_list", ctypes.POINTER(ctypes.c_int)), ("c_snk", ctypes.POINTER(ctypes.c_double)),
+                ("c_src", ctypes.POINTER(ctypes.c_double)), ("flav_snk", ctypes.c_int * 3),
+                ("flav_src", ctypes.c_int * 3)]
+
+
 _vp = ctypes.c_void_p
 _sig = {
     "laph_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp)]),
@@ -97,6 +110,21 @@ _sig = {
     "laph_sinks": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "correlate": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
     "correlate_noalloc": (ctypes.c_int, [ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp]),
+    "laph_mom_overlaps": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                         _vp]),
+    "correlate_mom": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp, _vp,
+                                     _vp]),
+    "laph_meson_loops": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(CorrSpec), _vp, _vp, _vp,
+                                        ctypes.c_int, _vp, _vp]),
+    "correlate_disconnected": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                              ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "laph_displaced_overlaps": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, _vp, ctypes.c_int, _vp, ctypes.c_int,
+                                               _vp, ctypes.c_int, _vp, _vp, _vp]),
+    "correlate_pipi": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(PipiSpec), _vp, _vp, _vp, _vp, _vp,
+                                      _vp, _vp, _vp]),
+    "laph_baryon_tensor": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.c_int, _vp, _vp, _vp]),
+    "correlate_baryon": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), ctypes.POINTER(BaryonSpec), _vp, _vp, _vp, _vp,
+                                        _vp]),
     "laph_precond_size": (ctypes.c_int, []),
     "laph_precond_init": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_double, _vp]),
     "laph_precond_train": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), _vp, _vp,
@@ -322,3 +350,83 @@ def correlate_noalloc(lat, channel, t0, nv, dil, b_list, coefs, noises, corr, st
     cp = (_vp * len(coefs))(*[_ptr(c) for c in coefs])
     npt = (_vp * len(noises))(*[_ptr(n) for n in noises])
     _check(_lib.correlate_noalloc(ctypes.byref(lat), ctypes.byref(spec), cp, npt, _ptr(corr), _stream(stream)))
+
+
+def _spec(channel, t0, nv, dil, b_list):
+    b = np.ascontiguousarray(np.asarray(b_list, dtype=np.int32))
+    return CorrSpec(int(channel), int(t0), int(nv), dil, len(b), b.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), b
+
+
+def laph_mom_overlaps(ctx, lat, evecs, nv, moms, phi, stream=None):
+    """phi[nmom][nt][nv][nv] = V^dag e^{-ip.x} V for the integer momenta in moms."""
+    m = np.ascontiguousarray(np.asarray(moms, dtype=np.int32).reshape(-1, 3))
+    _check(_lib.laph_mom_overlaps(ctx.ptr, ctypes.byref(lat), _ptr(evecs), int(nv), int(m.shape[0]), _ptr(m),
+                                  _ptr(phi), _stream(stream)))
+
+
+def correlate_mom(ctx, lat, channel, t0, nv, dil, b_list, coefs, noises, phi, corr, stream=None):
+    spec, _b = _spec(channel, t0, nv, dil, b_list)
+    cp = (_vp * 2)(*[_ptr(c) for c in coefs])
+    npt = (_vp * 2)(*[_ptr(n) for n in noises])
+    _check(_lib.correlate_mom(ctx.ptr, ctypes.byref(lat), ctypes.byref(spec), cp, npt, _ptr(phi), _ptr(corr),
+                              _stream(stream)))
+
+
+def laph_meson_loops(ctx, lat, channel, nv, dil, b_list, coef, noise, phi, reverse, loops, stream=None):
+    spec, _b = _spec(channel, 0, nv, dil, b_list)
+    _check(_lib.laph_meson_loops(ctx.ptr, ctypes.byref(lat), ctypes.byref(spec), _ptr(coef), _ptr(noise), _ptr(phi),
+                                 int(reverse), _ptr(loops), _stream(stream)))
+
+
+def correlate_disconnected(ctx, lat, t0, nc, loops1, loops2, vev, corr, stream=None):
+    _check(_lib.correlate_disconnected(ctx.ptr, ctypes.byref(lat), int(t0), int(nc), _ptr(loops1), _ptr(loops2),
+                                       float(np.real(vev)), float(np.imag(vev)), _ptr(corr), _stream(stream)))
+
+
+def laph_displaced_overlaps(ctx, lat, links3d, evecs, nv, mom, path_bar, path, phi, stream=None):
+    """phi[nt][nv][nv] = Phi_{p,jk}: qbar displaced along path_bar, q along path (signed steps)."""
+    m = np.ascontiguousarray(np.asarray(mom, dtype=np.int32).reshape(3))
+    pb = np.ascontiguousarray(np.asarray(path_bar, dtype=np.int32).reshape(-1))
+    pk = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1))
+    _check(_lib.laph_displaced_overlaps(ctx.ptr, ctypes.byref(lat), _ptr(links3d), _ptr(evecs), int(nv), _ptr(m),
+                                        int(pb.size), _ptr(pb) if pb.size else None, int(pk.size),
+                                        _ptr(pk) if pk.size else None, _ptr(phi), _stream(stream)))
+
+
+def laph_baryon_tensor(ctx, lat, evecs, nv, mom, T, stream=None):
+    """T[nt][nv][nv][nv] = sum_x e^{-ip.x} eps_abc V_n1(x)_a V_n2(x)_b V_n3(x)_c for the integer momentum mom."""
+    m = np.ascontiguousarray(np.asarray(mom, dtype=np.int32).reshape(3))
+    _check(_lib.laph_baryon_tensor(ctx.ptr, ctypes.byref(lat), _ptr(evecs), int(nv), _ptr(m), _ptr(T),
+                                   _stream(stream)))
+
+
+def correlate_baryon(ctx, lat, t0, nv, dil, b_list, c_snk, c_src, flav_snk, flav_src, coefs, noises, T, corr,
+                     stream=None):
+    """Eq. (baryoncorr) for three lines; c_snk, c_src are [4][4][4] complex spin tensors, flav_* three labels."""
+    b = np.ascontiguousarray(np.asarray(b_list, dtype=np.int32))
+    cs = np.ascontiguousarray(np.asarray(c_snk, dtype=np.complex128).reshape(64)).view(np.float64)
+    cr = np.ascontiguousarray(np.asarray(c_src, dtype=np.complex128).reshape(64)).view(np.float64)
+    dptr = ctypes.POINTER(ctypes.c_double)
+    spec = BaryonSpec(int(t0), int(nv), dil, len(b), b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      cs.ctypes.data_as(dptr), cr.ctypes.data_as(dptr), (ctypes.c_int * 3)(*map(int, flav_snk)),
+                      (ctypes.c_int * 3)(*map(int, flav_src)))
+    cp = (_vp * 3)(*[_ptr(c) for c in coefs])
+    npt = (_vp * 3)(*[_ptr(n) for n in noises])
+    _check(_lib.correlate_baryon(ctx.ptr, ctypes.byref(lat), ctypes.byref(spec), cp, npt, _ptr(T), _ptr(corr),
+                                 _stream(stream)))
+
+
+def correlate_pipi(ctx, lat, iso, iso3, t0, nv, dil_fwd, b_fwd, coef_fwd, noise_fwd, dil_smt=None, b_smt=(),
+                   coef_smt=(), noise_smt=(), phi_p=None, phi_mp=None, corr=None, stream=None):
+    """Two-pion correlator |I, I3> (pions of momenta p, -p) from four forward and two same-time lines."""
+    bf = np.ascontiguousarray(np.asarray(b_fwd, dtype=np.int32))
+    bs = np.ascontiguousarray(np.asarray(b_smt, dtype=np.int32).reshape(-1))
+    ip = ctypes.POINTER(ctypes.c_int)
+    spec = PipiSpec(int(iso), int(iso3), int(t0), int(nv), dil_fwd, len(bf), bf.ctypes.data_as(ip),
+                    dil_smt if dil_smt is not None else Dilution(), len(bs), bs.ctypes.data_as(ip) if bs.size else None)
+    cf = (_vp * 4)(*[_ptr(c) for c in coef_fwd])
+    nf = (_vp * 4)(*[_ptr(n) for n in noise_fwd])
+    cs = (_vp * 2)(*[_ptr(c) for c in coef_smt]) if len(coef_smt) else None
+    ns = (_vp * 2)(*[_ptr(n) for n in noise_smt]) if len(noise_smt) else None
+    _check(_lib.correlate_pipi(ctx.ptr, ctypes.byref(lat), ctypes.byref(spec), cf, nf, cs, ns, _ptr(phi_p),
+                               _ptr(phi_mp), _ptr(corr), _stream(stream)))

@@ -119,6 +119,38 @@ def test_learned_solve_and_gain(trained):
     assert fell["untrained"] or its["trained"] < its["untrained"], (its, fell)
 
 
+def test_learned_fgcr_vs_mixed_bicgstab(trained):
+    """What the trained network gains over the method without it, on right-hand sides it was
+    not trained on: learned FGCR against the mixed batched BiCGStab (the production solver), both
+    inside the same FP64 defect correction to 1e-10.  Counted in stencil hops: an FGCR step
+    applies the full K once (two even-odd hops) and the network once; a BiCGStab iteration
+    applies the Schur operator twice (four hops).  The network cuts the hops; its own cost, one
+    application per FGCR step, is what makes the learned solve slower in time, and the test
+    reports both (printed) without asserting on time."""
+    import time
+    import torch
+    L = lib()
+    wl, ref, lat, u = trained["wl"], trained["ref"], trained["lat"], trained["u"]
+    b = dev(synth.random_spinor(wl.ns, wl.nt, seed=557, nrhs=8))
+    out = {}
+    for name, prm in (("learned", L.solver_params(mode=L.LEARNED, weights=dev(trained["w"]), tol=1e-10, rhs_block=8)),
+                      ("mixed", L.solver_params(mode=L.MIXED_FP32, tol=1e-10, rhs_block=8))):
+        sol = torch.empty_like(b)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        reps = L.dirac_solve_batch(context(), lat, u, wl.m0, wl.csw, b, sol, 8, prm)
+        torch.cuda.synchronize()
+        out[name] = dict(s=time.perf_counter() - t, iters=max(r.iters for r in reps),
+                         fell=any(r.fallback_used for r in reps), resid=max(r.true_resid for r in reps))
+    assert out["learned"]["resid"] <= 1e-10 and out["mixed"]["resid"] <= 1e-10
+    assert not out["learned"]["fell"]
+    hops_learned, hops_mixed = 2 * out["learned"]["iters"], 4 * out["mixed"]["iters"]
+    print(f"learned FGCR: {out['learned']['iters']} steps = {hops_learned} hops + {out['learned']['iters']} network "
+          f"applications, {out['learned']['s']:.3f} s; mixed BiCGStab: {out['mixed']['iters']} iterations = "
+          f"{hops_mixed} hops, {out['mixed']['s']:.3f} s")
+    assert hops_learned < hops_mixed, out
+
+
 def test_stalled_learned_cycle_falls_back(trained):
     """A network that outputs zero makes every learned cycle stall (a host-side injected
     failure); the plain mixed solver takes over and the answer still converges."""
