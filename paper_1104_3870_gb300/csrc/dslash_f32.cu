@@ -217,6 +217,9 @@ __global__ void __launch_bounds__(128, MODE == HOP_APPLY ? 6 : 8) hop2_kernel(co
 // refilled with job n+NS as soon as every lane has read it.  Lane 0 issues all copies, so a
 // job costs the warp a handful of instructions, and warps never wait on one another.
 constexpr int HOP3_WARPS = 4;
+#ifndef HOP3_MINB
+#define HOP3_MINB 4   // blocks per SM the register allocation targets
+#endif
 // RPT right-hand sides per lane: a warp owns 32 RPT RHS of its site; the tile of a hop is
 // 12 rows x 256 RPT B, followed by the link (144 B) or the clover block (576 B).
 // HPJ hops per job: 1, or 2 (the forward and backward hop of one direction: two tiles and two links
@@ -236,7 +239,7 @@ __device__ int g_hop3_timeout;   // set when a copy wait gives up (or the ring i
 // products <out, z> and <out, out> of the warp's sites in FP32 and writes them as the warp's
 // partial sums partial[warp][k][r] (k = 0, 1; FP64) for a fixed-order final sum.
 template <int MODE, int NS, int RPT, int DOTS = 0, typename E = float2, int HPJ = 1>
-__global__ void __launch_bounds__(HOP3_WARPS * 32, 4)
+__global__ void __launch_bounds__(HOP3_WARPS * 32, HOP3_MINB)
     hop3_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_z,
                 const int *__restrict__ nbr, const int *__restrict__ order, const float4 *__restrict__ L,
                 const float *__restrict__ C, int Vh, int p, float hws, float hwt, E *__restrict__ out, int nr, int gshift,
