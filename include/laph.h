@@ -297,6 +297,12 @@ int laph_precond_grad(laph_ctx *ctx, const laph_lattice *lat, const void *links,
 /* out = N(in) for nrhs fields (c128). */
 int laph_precond_apply(laph_ctx *ctx, const laph_lattice *lat, const void *links, const laph_dirac_params *dirac,
                        const float *weights, const void *in, void *out, int nrhs, void *stream);
+/* The same network with its layers on the tensor cores (tcgen05; transported inputs and
+ * weights rounded to BF16, FP32 accumulation), as the learned solver applies it inside FGCR
+ * (LAPH_NN_FP32=1 in the environment keeps that solver on the FP32 layers).  nrhs a multiple
+ * of 32 (LAPH_ERR_ARG otherwise). */
+int laph_precond_apply_tc(laph_ctx *ctx, const laph_lattice *lat, const void *links, const laph_dirac_params *dirac,
+                          const float *weights, const void *in, void *out, int nrhs, void *stream);
 
 /* Applies K (FP64) to nrhs fields: out = K in (layouts as dirac_solve_batch). */
 int laph_dirac_apply(laph_ctx *ctx, const laph_lattice *lat, const void *links,

@@ -13,6 +13,7 @@
 // field f is f + c * 2 Vh 12 nr, parity p at + p Vh 12 nr, then [cb][12][nr].
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "blas.cuh"
@@ -22,6 +23,12 @@
 namespace laph {
 
 constexpr int NN_MAXC = 4;
+
+// tensor-core layers (nn_tc.cu): nr a multiple of 32
+bool nn_tc_ok(int nr, int cin, int cout);
+void nn_layer_tensor_core(laph_ctx *ctx, const DiracOp &op, long Vh, int nr, int cin, int cout, const float2 *W,
+                          const float2 *in, float2 *out, cudaStream_t s);
+void nn_tc_check(cudaStream_t s);
 
 struct NNShape {
     int nchan = 4, nlayers = 4;
@@ -316,10 +323,15 @@ struct Net {
     const DiracOp *op;
     long Vh;
     int nr;
+    laph_ctx *tc = nullptr;   // non-null: the layers run on the tensor cores (nn_tc.cu) where they can
 };
 
 static void launch_layer(const Net &net, int cin, int cout, const float2 *W, const float2 *in, float2 *out,
                          cudaStream_t s) {
+    if (net.tc != nullptr && nn_tc_ok(net.nr, cin, cout)) {
+        nn_layer_tensor_core(net.tc, *net.op, net.Vh, net.nr, cin, cout, W, in, out, s);
+        return;
+    }
     long n = 2 * net.Vh * net.nr * cout;
     size_t shm = sizeof(float4) * 9 * cin * cout * 16;
     if (shm > 48 * 1024) LAPH_CUDA(cudaFuncSetAttribute(nn_layer2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
@@ -518,7 +530,13 @@ void solve_block_learned(laph_ctx *ctx, const DiracOp &op, const float *weights,
     LAPH_CUDA(cudaMemsetAsync(xo, 0, hb, s));
     LAPH_CUDA(cudaMemcpyAsync(re, be, hb, cudaMemcpyDeviceToDevice, s));
     LAPH_CUDA(cudaMemcpyAsync(ro, bo, hb, cudaMemcpyDeviceToDevice, s));
-    Net net{NNShape(), &op, g.Vh, nr};
+    // inside FGCR the network runs on the tensor cores (BF16 operands; the flexible method takes an
+    // inexact preconditioner); LAPH_NN_FP32=1 keeps the FP32 CUDA-core layers
+    static const bool nn_fp32 = [] {
+        const char *e = std::getenv("LAPH_NN_FP32");
+        return e != nullptr && e[0] == '1';
+    }();
+    Net net{NNShape(), &op, g.Vh, nr, nn_fp32 ? nullptr : ctx};
     const int restart = prm.gcr_restart > 0 ? prm.gcr_restart : 16;
     int total = 0;
     double prev_worst = 1e300;
@@ -575,6 +593,7 @@ void solve_block_learned(laph_ctx *ctx, const DiracOp &op, const float *weights,
         mrhs_copy_scaled<double, float>(rows, nr, scale, ro, (c32 *)(b32 + half), s);
         double want = std::max(prm.inner_tol, 0.2 * prm.tol / std::max(worst, prm.tol));
         int n = fgcr(ctx, net, (const float2 *)weights, b32, x32, want, std::max(1, prm.maxiter - total), restart, s);
+        if (net.tc != nullptr) nn_tc_check(s);
         total += n;
         for (int k = 0; k < nr; ++k)
             if (hsc[k] > 0) {
@@ -790,11 +809,11 @@ extern "C" int laph_precond_grad(laph_ctx *ctx, const laph_lattice *lat, const v
     });
 }
 
-// Applies the network: out = N(in) for nrhs full fields (ABI layout, c128 in and out).
-extern "C" int laph_precond_apply(laph_ctx *ctx, const laph_lattice *lat, const void *links,
-                                  const laph_dirac_params *dirac, const float *weights, const void *in, void *out,
-                                  int nrhs, void *stream) {
-    return guard([&] {
+// Applies the network: out = N(in) for nrhs full fields (ABI layout, c128 in and out); tc: the
+// layers on the tensor cores (nrhs a multiple of 32).
+static void precond_apply(laph_ctx *ctx, const laph_lattice *lat, const void *links, const laph_dirac_params *dirac,
+                          const float *weights, const void *in, void *out, int nrhs, void *stream, bool tc) {
+    {
         ctx_activate(ctx);
         Geom g = make_geom(lat);
         LAPH_REQUIRE(nrhs >= 1 && nrhs <= 256, "nrhs must be 1..256");
@@ -807,7 +826,8 @@ extern "C" int laph_precond_apply(laph_ctx *ctx, const laph_lattice *lat, const 
         const float2 *W = (const float2 *)stage_in(ctx, weights, sizeof(float2) * nw, "nn_apply_w", s);
         StagedOut o = stage_out(ctx, out, fb, "nn_apply_out");
         DiracOp op = prepare_dirac(ctx, g, L, dirac->m0, dirac->csw, lat->xi, s);
-        Net net{sh, &op, g.Vh, nrhs};
+        if (tc) LAPH_REQUIRE(nn_tc_ok(nrhs, 1, 1), "tensor-core network: nrhs must be a multiple of 32");
+        Net net{sh, &op, g.Vh, nrhs, tc ? ctx : nullptr};
         const long chan = 2 * g.Vh * 12 * (long)nrhs;
         std::vector<float2 *> acts(sh.nlayers + 1);
         for (int l = 0; l <= sh.nlayers; ++l)
@@ -824,5 +844,18 @@ extern "C" int laph_precond_apply(laph_ctx *ctx, const laph_lattice *lat, const 
         mrhs_copy_scaled<float, double>(rows, nrhs, ones, (const c32 *)(acts[sh.nlayers] + g.Vh * 12 * (long)nrhs), to, s);
         eo_to_fields(g, te, to, 0, nrhs, (c64 *)o.dev, s);
         o.commit(s);
-    });
+        if (tc) nn_tc_check(s);
+    }
+}
+
+extern "C" int laph_precond_apply(laph_ctx *ctx, const laph_lattice *lat, const void *links,
+                                  const laph_dirac_params *dirac, const float *weights, const void *in, void *out,
+                                  int nrhs, void *stream) {
+    return guard([&] { precond_apply(ctx, lat, links, dirac, weights, in, out, nrhs, stream, false); });
+}
+
+extern "C" int laph_precond_apply_tc(laph_ctx *ctx, const laph_lattice *lat, const void *links,
+                                     const laph_dirac_params *dirac, const float *weights, const void *in, void *out,
+                                     int nrhs, void *stream) {
+    return guard([&] { precond_apply(ctx, lat, links, dirac, weights, in, out, nrhs, stream, true); });
 }

@@ -134,6 +134,8 @@ _sig = {
                                          ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
     "laph_precond_apply": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), _vp, _vp, _vp,
                                           ctypes.c_int, _vp]),
+    "laph_precond_apply_tc": (ctypes.c_int, [_vp, ctypes.POINTER(Lattice), _vp, ctypes.POINTER(DiracParams), _vp, _vp, _vp,
+                                          ctypes.c_int, _vp]),
     "laph_launch_count": (ctypes.c_long, []),
     "laph_profile_enable": (None, [ctypes.c_int]),
     "laph_profile_families": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
@@ -339,6 +341,11 @@ def laph_precond_grad(ctx, lat, links, m0, csw, weights, rho, phi, npairs, grad,
 
 def laph_precond_apply(ctx, lat, links, m0, csw, weights, inp, out, nrhs, stream=None):
     _check(_lib.laph_precond_apply(ctx.ptr, ctypes.byref(lat), _ptr(links), ctypes.byref(DiracParams(m0, csw)),
+                                   _ptr(weights), _ptr(inp), _ptr(out), int(nrhs), _stream(stream)))
+
+
+def laph_precond_apply_tc(ctx, lat, links, m0, csw, weights, inp, out, nrhs, stream=None):
+    _check(_lib.laph_precond_apply_tc(ctx.ptr, ctypes.byref(lat), _ptr(links), ctypes.byref(DiracParams(m0, csw)),
                                    _ptr(weights), _ptr(inp), _ptr(out), int(nrhs), _stream(stream)))
 
 

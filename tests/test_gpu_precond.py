@@ -5,7 +5,11 @@ the plain solver when the learned cycle stalls.
 
 Tolerances: FP32 network output rel <= 2e-5; gradients rel <= 2e-4 per layer
 (FP32 forward, FP32 partial sums, FP64 totals); solves as everywhere else
-(FP64 true residual <= 1e-10, ||x - x_LU|| / ||x_LU|| <= 1e-8).
+(FP64 true residual <= 1e-10, ||x - x_LU|| / ||x_LU|| <= 1e-8).  The tensor-core
+network (BF16 transported inputs and weights, FP32 accumulation): each layer rounds
+its inputs and weights to 8 significant bits (relative 2^-9 each), so an output
+carries about 2^-8 of the terms it sums per layer; over four layers the bound is
+rel <= 2e-2 per right-hand side in the 2-norm against the FP32 network.
 """
 import numpy as np
 import pytest
@@ -44,6 +48,39 @@ def test_apply_matches_oracle(small):
     for i in range(3):
         ref = precond.apply(u, ws, x[i])
         assert np.linalg.norm(got[i] - ref) / np.linalg.norm(ref) < 2e-5
+
+
+@pytest.mark.parametrize("nrhs", [32, 64])
+def test_apply_tc_matches_fp32_network(small, nrhs):
+    """laph_precond_apply_tc (layers on the tensor cores) against the FP32 layers, which are
+    themselves pinned to the oracle above; 64 right-hand sides run two units per site."""
+    import torch
+    L = lib()
+    u, ws = small
+    lat = L.lattice(4, 8, 3.5)
+    x = dev(synth.random_spinor(4, 8, seed=8, nrhs=nrhs))
+    w = dev(_weights_from(ws))
+    ref = empty(x.shape, torch.complex128)
+    got = empty(x.shape, torch.complex128)
+    L.laph_precond_apply(context(), lat, dev(u), -0.05, 1.0, w, x, ref, nrhs)
+    L.laph_precond_apply_tc(context(), lat, dev(u), -0.05, 1.0, w, x, got, nrhs)
+    r, g = host(ref), host(got)
+    rel = np.array([np.linalg.norm(g[i] - r[i]) / np.linalg.norm(r[i]) for i in range(nrhs)])
+    assert rel.max() <= 2e-2, rel.max()
+    assert rel.min() > 1e-6   # the BF16 path ran (it cannot match FP32 to rounding)
+    # one right-hand side against the oracle as well
+    o = precond.apply(u, ws, host(x)[nrhs - 1])
+    assert np.linalg.norm(g[nrhs - 1] - o) / np.linalg.norm(o) <= 2e-2
+
+
+def test_apply_tc_rejects_ragged_block(small):
+    import torch
+    L = lib()
+    u, ws = small
+    x = dev(synth.random_spinor(4, 8, seed=9, nrhs=3))
+    out = empty(x.shape, torch.complex128)
+    with pytest.raises(L.LaphError):
+        L.laph_precond_apply_tc(context(), L.lattice(4, 8, 3.5), dev(u), -0.05, 1.0, dev(_weights_from(ws)), x, out, 3)
 
 
 def test_gradients_match_oracle(small):
@@ -119,36 +156,56 @@ def test_learned_solve_and_gain(trained):
     assert fell["untrained"] or its["trained"] < its["untrained"], (its, fell)
 
 
-def test_learned_fgcr_vs_mixed_bicgstab(trained):
+@pytest.mark.parametrize("nb", [8, 32])
+def test_learned_fgcr_vs_mixed_bicgstab(trained, nb):
     """What the trained network gains over the method without it, on right-hand sides it was
     not trained on: learned FGCR against the mixed batched BiCGStab (the production solver), both
     inside the same FP64 defect correction to 1e-10.  Counted in stencil hops: an FGCR step
     applies the full K once (two even-odd hops) and the network once; a BiCGStab iteration
     applies the Schur operator twice (four hops).  The network cuts the hops; its own cost, one
     application per FGCR step, is what makes the learned solve slower in time, and the test
-    reports both (printed) without asserting on time."""
+    reports both (printed) without asserting on time.  Blocks of 8 run the FP32 network layers,
+    blocks of 32 the tensor-core layers."""
     import time
     import torch
     L = lib()
     wl, ref, lat, u = trained["wl"], trained["ref"], trained["lat"], trained["u"]
-    b = dev(synth.random_spinor(wl.ns, wl.nt, seed=557, nrhs=8))
+    b = dev(synth.random_spinor(wl.ns, wl.nt, seed=557, nrhs=nb))
     out = {}
-    for name, prm in (("learned", L.solver_params(mode=L.LEARNED, weights=dev(trained["w"]), tol=1e-10, rhs_block=8)),
-                      ("mixed", L.solver_params(mode=L.MIXED_FP32, tol=1e-10, rhs_block=8))):
+    for name, prm in (("learned", L.solver_params(mode=L.LEARNED, weights=dev(trained["w"]), tol=1e-10, rhs_block=nb)),
+                      ("mixed", L.solver_params(mode=L.MIXED_FP32, tol=1e-10, rhs_block=nb))):
         sol = torch.empty_like(b)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        reps = L.dirac_solve_batch(context(), lat, u, wl.m0, wl.csw, b, sol, 8, prm)
+        reps = L.dirac_solve_batch(context(), lat, u, wl.m0, wl.csw, b, sol, nb, prm)
         torch.cuda.synchronize()
         out[name] = dict(s=time.perf_counter() - t, iters=max(r.iters for r in reps),
                          fell=any(r.fallback_used for r in reps), resid=max(r.true_resid for r in reps))
     assert out["learned"]["resid"] <= 1e-10 and out["mixed"]["resid"] <= 1e-10
     assert not out["learned"]["fell"]
     hops_learned, hops_mixed = 2 * out["learned"]["iters"], 4 * out["mixed"]["iters"]
-    print(f"learned FGCR: {out['learned']['iters']} steps = {hops_learned} hops + {out['learned']['iters']} network "
+    print(f"{nb} RHS: learned FGCR: {out['learned']['iters']} steps = {hops_learned} hops + {out['learned']['iters']} network "
           f"applications, {out['learned']['s']:.3f} s; mixed BiCGStab: {out['mixed']['iters']} iterations = "
           f"{hops_mixed} hops, {out['mixed']['s']:.3f} s")
     assert hops_learned < hops_mixed, out
+
+
+def test_learned_solve_tensor_core_network(trained):
+    """A block of 32 right-hand sides: FGCR applies the network on the tensor cores; the FP64
+    defect correction still brings every solution to the dense-LU answer."""
+    import torch
+    L = lib()
+    wl, ref, lat, u = trained["wl"], trained["ref"], trained["lat"], trained["u"]
+    b = synth.random_spinor(wl.ns, wl.nt, seed=558, nrhs=32)
+    sol = torch.empty_like(dev(b))
+    reps = L.dirac_solve_batch(context(), lat, u, wl.m0, wl.csw, dev(b), sol, 32,
+                               L.solver_params(mode=L.LEARNED, weights=dev(trained["w"]), tol=1e-10, rhs_block=32))
+    x_lu, _ = ref.solve(b[:4], "lu")
+    x = host(sol)
+    assert max(r.true_resid for r in reps) <= 1e-10
+    assert not any(r.fallback_used for r in reps)
+    for i in range(4):
+        assert np.linalg.norm(x[i] - x_lu[i]) / np.linalg.norm(x_lu[i]) < 1e-8
 
 
 def test_stalled_learned_cycle_falls_back(trained):
