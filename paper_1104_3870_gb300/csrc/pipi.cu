@@ -48,13 +48,14 @@ namespace {
 enum LineKind { FWD = 0, BWD = 1, SMT = 2 };
 
 // Same-time line gathered per slice: phi[t][j] = coef[bidx[t][j]][t], rho[t][j] = the diluted
-// noise of projector bidx[t][j] on slice t ([nt][nbt][4][nv] each).
-__global__ void smt_gather_kernel(int nt, int nbt, int nv, const int *__restrict__ bidx, const int *__restrict__ bpos,
-                                  const c64 *__restrict__ coef, const uint8_t *__restrict__ codes,
-                                  const uint8_t *__restrict__ mask, c64 *__restrict__ phi, c64 *__restrict__ rho) {
+// noise of projector bidx[t][j] on slice t ([nt][nbt][4][nv] each); bidx indexes the line's
+// projector list (its coefficients and its masks).
+__global__ void smt_gather_kernel(int nt, int nbt, int nv, const int *__restrict__ bidx, const c64 *__restrict__ coef,
+                                  const uint8_t *__restrict__ codes, const uint8_t *__restrict__ mask,
+                                  c64 *__restrict__ phi, c64 *__restrict__ rho) {
     const int t = blockIdx.x, j = blockIdx.y;
-    const int b = bidx[t * nbt + j], pos = bpos[t * nbt + j];
-    const uint8_t *m = mask + (long)pos * (nt + 4 + nv);
+    const int b = bidx[t * nbt + j];
+    const uint8_t *m = mask + (long)b * (nt + 4 + nv);
     for (int e = threadIdx.x; e < 4 * nv; e += blockDim.x) {
         const int a = e / nv, n = e % nv;
         phi[((long)t * nbt + j) * 4 * nv + e] = coef[((long)b * nt + t) * 4 * nv + e];
@@ -305,13 +306,12 @@ extern "C" int correlate_pipi(laph_ctx *ctx, const laph_lattice *lat, const laph
             LAPH_REQUIRE(nbs >= 1 && spec->b_smt != nullptr && coef_smt != nullptr && noise_smt != nullptr,
                          "this isospin needs same-time lines");
             std::vector<uint8_t> ms = dilution_masks(spec->dil_smt, nt, nv, spec->b_smt, nbs);
-            std::vector<int> bidx, bpos;
+            std::vector<int> bidx;
             for (int t = 0; t < nt; ++t) {
                 int cnt = 0;
                 for (int j = 0; j < nbs; ++j)
                     if (ms[(size_t)j * (nt + 4 + nv) + t]) {
                         bidx.push_back(j);
-                        bpos.push_back(j);
                         ++cnt;
                     }
                 if (t == 0) nbt = cnt;
@@ -320,10 +320,8 @@ extern "C" int correlate_pipi(laph_ctx *ctx, const laph_lattice *lat, const laph
             }
             uint8_t *dms = (uint8_t *)ws_get(ctx, "pp:masks", ms.size());
             LAPH_CUDA(cudaMemcpyAsync(dms, ms.data(), ms.size(), cudaMemcpyHostToDevice, s));
-            int *dix = (int *)ws_get(ctx, "pp:bidx", sizeof(int) * 2 * bidx.size());
+            int *dix = (int *)ws_get(ctx, "pp:bidx", sizeof(int) * bidx.size());
             LAPH_CUDA(cudaMemcpyAsync(dix, bidx.data(), sizeof(int) * bidx.size(), cudaMemcpyHostToDevice, s));
-            LAPH_CUDA(cudaMemcpyAsync(dix + bidx.size(), bpos.data(), sizeof(int) * bpos.size(), cudaMemcpyHostToDevice,
-                                      s));
             for (int k = 0; k < 2; ++k) {
                 LAPH_REQUIRE(coef_smt[k] != nullptr && noise_smt[k] != nullptr, "same-time line arrays are null");
                 const std::string id = std::to_string(k);
@@ -332,8 +330,7 @@ extern "C" int correlate_pipi(laph_ctx *ctx, const laph_lattice *lat, const laph
                 const uint8_t *codes = (const uint8_t *)stage_in(ctx, noise_smt[k], (size_t)nt * 4 * nv, "pp:ns" + id, s);
                 phs[k] = (c64 *)ws_get(ctx, "pp:ps" + id, sizeof(c64) * (size_t)nt * nbt * 4 * nv);
                 rhs_[k] = (c64 *)ws_get(ctx, "pp:rs" + id, sizeof(c64) * (size_t)nt * nbt * 4 * nv);
-                smt_gather_kernel<<<dim3(nt, nbt), 128, 0, s>>>(nt, nbt, nv, dix, dix + bidx.size(), cs, codes, dms,
-                                                               phs[k], rhs_[k]);
+                smt_gather_kernel<<<dim3(nt, nbt), 128, 0, s>>>(nt, nbt, nv, dix, cs, codes, dms, phs[k], rhs_[k]);
                 LAPH_LAUNCH_CHECK();
             }
         }

@@ -93,3 +93,57 @@ def test_sinks_sampled_definition(medium):
         x = medium["sol"][i].reshape(wl.nt, -1, 4, 3)[t, :, a, :]
         ref = np.sum(V[t, n].conj() * x)
         assert abs(medium["coef"][i, t, a, n] - ref) <= 1e-12 * max(abs(ref), np.abs(medium["coef"][i]).max())
+
+
+@pytest.fixture(scope="module")
+def medium_lines():
+    """Synthetic lines at the medium workload's size (16^3 x 32, N_v = 32, the 32 projectors of
+    (TF, SF, LI8) whose time support holds t0 = 8): random orthonormal eigenvectors per slice,
+    seeded random sink coefficients, the oracle's noise for ids 0..3.  Both sides take these
+    inputs; the oracle builds site fields from them and contracts in site space."""
+    from oracle import laph as olaph
+    wl = synth.WORKLOADS["medium_16x32"]
+    dil = (wl.dil_time, wl.dil_spin, wl.dil_laph)
+    t0 = 8
+    nT, nS, nL = dl.counts(dil, wl.nt, wl.nv)
+    bs = [(bT * nS + bS) * nL + bL for bT in range(nT) if dl.projector_diag(dil[0][0], dil[0][1], wl.nt, bT)[t0]
+          for bS in range(nS) for bL in range(nL)]
+    v3 = wl.ns ** 3
+    g = synth.random_complex((wl.nt, 3 * v3, wl.nv), seed=71)
+    V = np.stack([np.linalg.qr(g[t])[0].T for t in range(wl.nt)]).reshape(wl.nt, wl.nv, v3, 3)
+    config_id = wl.gauge_seed % 65536
+    lines = []
+    for k in range(4):
+        coef = synth.random_complex((len(bs), wl.nt, 4, wl.nv), seed=80 + k)
+        codes = onoise.z4_codes(wl.nt, wl.nv, k, config_id)
+        rho = onoise.z4_values(codes)
+        line = olaph.Line.__new__(olaph.Line)
+        line.bs = list(bs)
+        line.varrho = np.stack([olaph.source(V, rho, dil, b) for b in bs])
+        # site fields sum_n V(t,n,x,c) coef(t,alpha,n), one matrix product per slice
+        vm = V.reshape(wl.nt, wl.nv, 3 * v3)
+        phi = np.einsum("btan,tnk->btak", coef, vm, optimize=True).reshape(len(bs), wl.nt, 4, v3, 3)
+        line.varphi = phi.transpose(0, 1, 3, 2, 4).reshape(len(bs), wl.nt, wl.ns, wl.ns, wl.ns, 4, 3)
+        lines.append((coef, codes, line))
+    return wl, dil, t0, bs, lines
+
+
+@pytest.mark.parametrize("channel", ["pion", "pipi"])
+def test_correlators_medium_size_vs_oracle(medium_lines, channel):
+    """correlate() at the medium size on synthetic lines against the oracle's site-space
+    contraction (Eq. (mesoncorr); I = 2 pi pi as D - X)                   1e-10 (floored)"""
+    import torch
+    from oracle import laph as olaph
+    L = lib()
+    wl, dil, t0, bs, lines = medium_lines
+    n = 4 if channel == "pipi" else 2
+    ch = {"pion": L.CH_PION, "rho": L.CH_RHO, "pipi": L.CH_PIPI_I2}[channel]
+    corr = empty((wl.nt,), torch.complex128)
+    L.correlate(context(), L.lattice(wl.ns, wl.nt, wl.xi), ch, t0, wl.nv, L.dilution(*dil), bs,
+                [dev(c) for c, _, _ in lines[:n]], [dev(k) for _, k, _ in lines[:n]], corr)
+    ol = [ln for _, _, ln in lines[:n]]
+    ref = olaph.pipi_i2(*ol, t0) if channel == "pipi" else olaph.meson_connected(ol[0], ol[1], t0, channel)
+    got = host(corr)
+    floor = 1e-3 * np.abs(ref).max()
+    assert np.abs(ref).max() > 0
+    assert np.all(np.abs(got - ref) <= 1e-10 * np.maximum(np.abs(ref), floor))
