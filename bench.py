@@ -71,6 +71,11 @@ def parse_args(argv=None):
     p.add_argument("--study-pairs", type=int, default=16, help="training pairs per training field")
     p.add_argument("--study-epochs", type=int, default=4, help="passes over all training fields")
     p.add_argument("--study-rhs", type=int, default=16, help="sources solved per held-out field")
+    p.add_argument("--nn-sweep", action="store_true",
+                   help="time one learned-network application (FP32 layers and tensor-core layers) against one "
+                        "application of K on the medium lattice instead of the path step")
+    p.add_argument("--nn-nr", type=int, default=64, help="right-hand sides of the network sweep")
+    p.add_argument("--nn-reps", type=int, default=3, help="timed repetitions of the network sweep")
     p.add_argument("--dslash-sweep", action="store_true", help="print the Dslash GB/s sweep instead of the path step")
     p.add_argument("--dslash-nr", default="1,8,16,32,64", help="right-hand-side counts of the Dslash sweep")
     p.add_argument("--dslash-iters", type=int, default=50, help="solver iterations per sweep point")
@@ -1001,6 +1006,63 @@ def run_dslash_sweep(args):
                       "rows": rows}), flush=True)
 
 
+def run_nn_sweep(args):
+    """One application of the learned network (laph_precond_apply: FP32 layers;
+    laph_precond_apply_tc: tensor-core layers) on nr random fields of the medium lattice, against
+    one application of K in the FP32 stencil (the two even-odd hops of laph_dslash_eo in the
+    apply mode), each the median of --nn-reps runs timed by CUDA events on the current stream.
+    The network calls include the ABI's layout conversion of their input and output."""
+    import torch
+    from paper_1104_3870_gb300 import build
+    build.build()
+    from paper_1104_3870_gb300 import laph as L
+    from paper_1104_3870_gb300.pipeline import LapHPath, LatticeSpec
+    import synth
+
+    wl = synth.WORKLOADS["medium_16x32"]
+    spec = LatticeSpec(wl.ns, wl.nt, wl.xi, wl.m0, wl.csw, wl.nv, (wl.dil_time, wl.dil_spin, wl.dil_laph),
+                       wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
+    path = LapHPath(spec, 0)
+    u, _ = path.prepare_links(wl.gauge())
+    nr = args.nn_nr
+    w = np.zeros(L.laph_precond_size(), dtype=np.float32)
+    L.laph_precond_init(7, wl.m0 + 1.0 + 3.0 / wl.xi, w)
+    wdev = torch.from_numpy(w).cuda()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    shape = (nr, wl.nt, wl.ns, wl.ns, wl.ns, 4, 3)
+    x = torch.complex(torch.randn(shape, dtype=torch.float64, device="cuda", generator=gen),
+                      torch.randn(shape, dtype=torch.float64, device="cuda", generator=gen))
+    y = torch.empty_like(x)
+    vh = wl.ns ** 3 * wl.nt // 2
+    xe = torch.randn((vh, 12, nr), dtype=torch.complex64, device="cuda")
+    ye = torch.empty_like(xe)
+    stream = torch.cuda.current_stream()
+
+    def med(fn):
+        ts = []
+        for _ in range(args.nn_reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ts = sorted(ts[1:])   # the first run includes one-time set-up
+        return ts[len(ts) // 2]
+
+    lat = path.lat
+    k_ms = med(lambda: [L.laph_dslash_eo(path.ctx, lat, u, wl.m0, wl.csw, p, L.HOP_APPLY, L.PREC_FP32, xe, xe, ye, nr)
+                        for p in (0, 1)])
+    fp32_ms = med(lambda: L.laph_precond_apply(path.ctx, lat, u, wl.m0, wl.csw, wdev, x, y, nr))
+    tc_ms = med(lambda: L.laph_precond_apply_tc(path.ctx, lat, u, wl.m0, wl.csw, wdev, x, y, nr))
+    print(json.dumps({"metric": "learned-network application vs K application (CUDA events, median)",
+                      "lattice": f"{wl.ns}^3x{wl.nt}", "nr": nr, "K_fp32_ms": k_ms, "network_fp32_ms": fp32_ms,
+                      "network_tc_ms": tc_ms, "fp32_in_K": fp32_ms / k_ms, "tc_in_K": tc_ms / k_ms}), flush=True)
+    path.close()
+
+
 def run_learned_study(args):
     """Learned preconditioner across gauge fields: fields are seeded 2000 + i on the medium
     lattice (the workload's smearing recipe and m0); the network is trained on (rho, phi =
@@ -1081,12 +1143,21 @@ def run_learned_study(args):
                           ("plain_fp64_bicgstab", L.solver_params(mode=L.PLAIN_FP64, rhs_block=1)),
                           ("mixed_bicgstab", L.solver_params(mode=L.MIXED_FP32, rhs_block=n))):
             sec, reps = timed(lambda: L.dirac_solve_batch(ctx, lat, u, wl.m0, wl.csw, b, x, n, prm))
-            row[name] = {"s": sec, "sources_per_s": n / sec, "iters_mean": float(np.mean([r.iters for r in reps])),
+            it = float(np.mean([r.iters for r in reps]))
+            # operator applications per source: an FGCR step applies K once and the network once; a
+            # BiCGStab iteration applies the even-odd Schur operator twice (four hops, two K's worth)
+            learned = name == "learned_fgcr"
+            row[name] = {"s": sec, "sources_per_s": n / sec, "iters_mean": it,
+                         "K_applications_mean": it if learned else 2.0 * it,
+                         "network_applications_mean": it if learned else 0.0,
+                         "network_layers": ("tensor cores" if n % 32 == 0 else "FP32") if learned else None,
                          "true_resid_max": max(r.true_resid for r in reps),
                          "fallback_used": int(sum(r.fallback_used for r in reps))}
         fields.append(row)
     agg = {k: {"sources_per_s": float(np.mean([r[k]["sources_per_s"] for r in fields])),
-               "iters_mean": float(np.mean([r[k]["iters_mean"] for r in fields]))}
+               "iters_mean": float(np.mean([r[k]["iters_mean"] for r in fields])),
+               "K_applications_mean": float(np.mean([r[k]["K_applications_mean"] for r in fields])),
+               "network_applications_mean": float(np.mean([r[k]["network_applications_mean"] for r in fields]))}
            for k in ("learned_fgcr", "plain_fp64_bicgstab", "mixed_bicgstab")}
     print(json.dumps({"metric": "learned preconditioner on held-out fields (diluted-source solves to 1e-10)",
                       "workload": f"{wl.name} lattice, fields seeded 2000..{2000 + nf - 1}, last {held} held out",
@@ -1103,7 +1174,9 @@ def run_learned_study(args):
 
 def main(argv=None):
     args = parse_args(argv)
-    if args.learned_study:
+    if args.nn_sweep:
+        run_nn_sweep(args)
+    elif args.learned_study:
         run_learned_study(args)
     elif args.dslash_sweep:
         run_dslash_sweep(args)
