@@ -133,4 +133,10 @@ WORKLOADS = {
                              gauge_seed=1002, dil_time=(DIL_INTERLACE, 16), dil_spin=(DIL_FULL, 0),
                              dil_laph=(DIL_INTERLACE, 8), source_times=(0,), n_noise=4,
                              target_iters=1500),
+    # The same lattice, field and mass with N_v = 112 (the eigenvector count of the paper's
+    # 24^3 x 128 runs, Sec. V), (TI16, SF, LI8): 512 diluted sources per noise as before.
+    "paper_24x128_nv112": Workload("paper_24x128_nv112", ns=24, nt=128, xi=3.5, csw=1.0, m0=-0.0003125, nv=112,
+                                   gauge_seed=1002, dil_time=(DIL_INTERLACE, 16), dil_spin=(DIL_FULL, 0),
+                                   dil_laph=(DIL_INTERLACE, 8), source_times=(0,), n_noise=4,
+                                   target_iters=1500),
 }

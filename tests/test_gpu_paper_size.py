@@ -7,6 +7,7 @@ tests/test_oracle_window.py) and every check is made on that slice:
 
   eigenpairs (a1)   slice 48 against scipy's eigsh at N_v = 64     eigenvalues rel <= 1e-10,
                                                                    eigenprojector <= 1e-8
+                    and at N_v = 112 (the paper's count at this size, Sec. V), the same bounds
   noise (a2)        the whole Z4 code table against the oracle's Philox     bit for bit
   sources (a2)      V^dag gamma_4 y_b on slice 48 equals P^(b) rho          <= 1e-12
   solves (a3)       for every source, slice 48 of the FP64 true residual y - K x under the
@@ -45,6 +46,12 @@ def paper():
     path = LapHPath(spec)
     u, ut = path.prepare_links(u0)
     evals, evecs, rep = path.eigvecs(ut)
+    import dataclasses
+    path112 = LapHPath(dataclasses.replace(spec, nv=112))
+    ev112, vec112, rep112 = path112.eigvecs(ut)
+    eig112 = dict(rep=rep112, evals=host(ev112[TS]), evecs=host(vec112[TS]))
+    del ev112, vec112
+    path112.close()
     bs = projectors_for_time(spec, 0)
     assert len(bs) == BLOCK
     rhs, codes = path.sources(evecs, 0, wl.config_id, bs)
@@ -52,7 +59,7 @@ def paper():
     coef = path.sinks(evecs, sol)
     torch.cuda.synchronize()
     bnorm = torch.linalg.vector_norm(rhs.reshape(BLOCK, -1), dim=1).cpu().numpy()
-    out = dict(wl=wl, spec=spec, bs=bs, rep=rep, reps=reps, bnorm=bnorm,
+    out = dict(wl=wl, spec=spec, bs=bs, rep=rep, reps=reps, bnorm=bnorm, eig112=eig112,
                evals=host(evals), evecs=host(evecs[TS]), codes=host(codes),
                rhs=host(rhs[:, TS]), sol=host(sol[:, TS - 1:TS + 2]), coef=host(coef[:, TS]))
     del rhs, sol, coef, evecs, u, ut
@@ -74,6 +81,14 @@ def test_eigenpairs_sampled_slice(paper):
     ev_g = paper["evals"][TS]
     assert np.abs(ev_g - ev_o[0]).max() <= 1e-10 * np.abs(ev_o).max()
     assert laplacian.eigenprojector_distance(paper["evecs"][None], vec_o) <= 1e-8
+
+
+def test_eigenpairs_sampled_slice_nv112(paper):
+    e = paper["eig112"]
+    assert e["rep"].nconv == 112 and e["rep"].max_resid <= 12 * 1e-13
+    ev_o, vec_o = laplacian.lowest_eigpairs(paper["utw"], 112, "sparse")
+    assert np.abs(e["evals"] - ev_o[0]).max() <= 1e-10 * np.abs(ev_o).max()
+    assert laplacian.eigenprojector_distance(e["evecs"][None], vec_o) <= 1e-8
 
 
 def test_noise_table_bit_exact(paper):
