@@ -34,6 +34,7 @@
 // projectors whose time support holds t contribute, so those are gathered first.  All FP64.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <map>
 #include <string>
 #include <tuple>
