@@ -60,6 +60,8 @@ def parse_args(argv=None):
                    help="run each step's stages one after another (default: the next batch's eigenvectors "
                         "overlap this batch's solves)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clock-sampler", action="store_true",
+                   help="do not run nvidia-smi beside the timed steps (for runs under a profiler)")
     p.add_argument("--inner-tol", type=float, default=None,
                    help="relative reduction each FP32 inner solve of the defect correction asks for (default: "
                         "3e-3 on the paper-shaped workload, where it measured fastest, else the library's 3e-4)")
@@ -569,7 +571,7 @@ def run_stream(args):
         st.run(u)
     torch.cuda.synchronize()
     barrier(world)
-    clocks = ClockSampler(local) if rank == 0 else None
+    clocks = ClockSampler(local) if rank == 0 and not args.no_clock_sampler else None
     L.laph_profile_enable(0)
     launches0 = L.laph_launch_count()
     t0, t1 = ev_pair()
@@ -747,7 +749,7 @@ def run_path(args):
         step(u, ut)
     torch.cuda.synchronize()
     barrier(world)
-    clocks = ClockSampler(local) if rank == 0 else None
+    clocks = ClockSampler(local) if rank == 0 and not args.no_clock_sampler else None
     L.laph_profile_reset()
     L.laph_profile_enable(1)
     launches0 = L.laph_launch_count()
