@@ -73,6 +73,7 @@ def parse_args(argv=None):
     p.add_argument("--learned-study", action="store_true",
                    help="print the held-out-field study of the learned preconditioner instead of the path step")
     p.add_argument("--study-fields", type=int, default=20, help="seeded fields (the last 4 held out)")
+    p.add_argument("--study-workload", default="medium_16x32", help="lattice, smearing recipe and mass of the study")
     p.add_argument("--study-pairs", type=int, default=16, help="training pairs per training field")
     p.add_argument("--study-epochs", type=int, default=4, help="passes over all training fields")
     p.add_argument("--study-rhs", type=int, default=16, help="sources solved per held-out field")
@@ -1093,7 +1094,7 @@ def run_learned_study(args):
     from paper_1104_3870_gb300.pipeline import LapHPath, LatticeSpec
     import synth
 
-    wl = synth.WORKLOADS[args.workload]
+    wl = synth.WORKLOADS[args.study_workload]
     spec = LatticeSpec(wl.ns, wl.nt, wl.xi, wl.m0, wl.csw, wl.nv, (wl.dil_time, wl.dil_spin, wl.dil_laph),
                        wl.rho_stout, wl.n_stout4d, wl.n_stout3d)
     path = LapHPath(spec, 0)
