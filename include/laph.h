@@ -490,7 +490,8 @@ int correlate_pipi(laph_ctx *ctx, const laph_lattice *lat, const laph_pipi_spec 
  *   three lines for which sink quark pi(s) has the flavour of source slot s.
  *   coef[k] = [nb][nt][4][nv] and noise[k] = [nt][4][nv] of line k (three lines,
  *   one noise each, the same nb, b_list and dilution), T from laph_baryon_tensor.
- *   corr [nt] c128.  Scratch about nt nv nb^2 (16 + nv/4) + nt nb^3 complex doubles.
+ *   corr [nt] c128.  Scratch: 16 nt nv nb^2 + 4 nt nv^2 nb + nt nb^3 complex doubles
+ *   (LAPH_ERR_NOMEM when the device cannot hold it).
  * ------------------------------------------------------------------------ */
 typedef struct {
     int t0;                   /* source time                                        */
