@@ -220,7 +220,7 @@ def oracle_sample(wl, seconds=15.0, threads=None, _cache={}):
 
 
 # ----------------------------------------------------------------------------- ncu traffic record
-HOP_KERNEL_VERSION = "hop3_tma_ns2_zblock8_pair"
+HOP_KERNEL_VERSION = "hop3_tma_ns2_zblock8_pair_cj"
 
 
 def measured_traffic_ratio(workload, family="dslash_fp32"):

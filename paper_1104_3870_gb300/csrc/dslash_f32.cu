@@ -224,13 +224,21 @@ constexpr int HOP3_WARPS = 4;
 // 12 rows x 256 RPT B, followed by the link (144 B) or the clover block (576 B).
 // HPJ hops per job: 1, or 2 (the forward and backward hop of one direction: two tiles and two links
 // per slot, five jobs per site instead of nine, each covering twice the copy latency).
-template <int RPT, typename E = float2, int HPJ = 1>
+// CJ (clover-inverse mode with two hops per job): the clover block rides in the last hop job, whose
+// slot the warp keeps until its epilogue, so a site takes four jobs instead of five.
+#ifndef HOP3_CLOVJ
+#define HOP3_CLOVJ 1
+#endif
+template <int RPT, typename E = float2, int HPJ = 1, bool CJ = false>
 struct Hop3Geo {
     static constexpr int SPIN = 12 * 32 * RPT * (int)sizeof(E);     // 3072 RPT B (FP32), 1536 RPT B (BF16)
-    static constexpr int BODY = HPJ * (SPIN + 144) > SPIN + 576 ? HPJ * (SPIN + 144) : SPIN + 576;
+    static constexpr int PAIRB = HPJ * (SPIN + 144) + (CJ ? 576 : 0);
+    static constexpr int BODY = PAIRB > SPIN + 576 ? PAIRB : SPIN + 576;
     static constexpr int SLOT = ((BODY + 127) / 128) * 128;         // 128-byte aligned slots
-    static constexpr int JOBS = 8 / HPJ + 1;                        // hop jobs + the epilogue job
+    static constexpr int JOBS = 8 / HPJ + (CJ ? 0 : 1);             // hop jobs (+ the epilogue job)
 };
+template <int MODE, int HPJ>
+__host__ __device__ constexpr bool hop3_cj() { return HOP3_CLOVJ && MODE == HOP_CLOVINV && HPJ == 2; }
 constexpr long long HOP3_WAIT_CYCLES = 1LL << 31;   // about one second at the maximum SM clock
 
 __device__ int g_hop3_timeout;   // set when a copy wait gives up (or the ring is misaligned); read by the host
@@ -245,8 +253,9 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, HOP3_MINB)
                 const float *__restrict__ C, int Vh, int p, float hws, float hwt, E *__restrict__ out, int nr, int gshift,
                 int nunits, c64 *__restrict__ partial, const uint32_t *__restrict__ rcode) {
     extern __shared__ __align__(128) unsigned char sm3[];
-    constexpr int HOP3_SPIN = Hop3Geo<RPT, E, HPJ>::SPIN, HOP3_SLOT = Hop3Geo<RPT, E, HPJ>::SLOT;
-    constexpr int NJ = Hop3Geo<RPT, E, HPJ>::JOBS;
+    constexpr bool CJ = hop3_cj<MODE, HPJ>();
+    constexpr int HOP3_SPIN = Hop3Geo<RPT, E, HPJ, CJ>::SPIN, HOP3_SLOT = Hop3Geo<RPT, E, HPJ, CJ>::SLOT;
+    constexpr int NJ = Hop3Geo<RPT, E, HPJ, CJ>::JOBS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (smem_u32(sm3) & 127) {   // tensor copies need 128-byte aligned destinations
         if (threadIdx.x == 0) atomicExch(&g_hop3_timeout, 2);
@@ -285,19 +294,21 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, HOP3_MINB)
             unsigned char *sl = ring + islot * HOP3_SLOT;
             uint64_t *b = bar + islot;
             fence_proxy_async_smem();
-            if (ij < NJ - 1) {
+            if (CJ || ij < NJ - 1) {
                 const int mu = HPJ == 2 ? ij : ij >> 1;
                 const float w = mu == 3 ? hwt : hws;
                 const int jn = e < 0 ? ~e : e;
                 meta[2 * islot] = e < 0 ? -w : w;
                 if (HPJ == 2) {
                     const int jb = e2 < 0 ? ~e2 : e2;
+                    const bool clov = CJ && ij == NJ - 1;
                     meta[2 * islot + 1] = e2 < 0 ? -w : w;
-                    mbar_arrive_expect_tx(b, 2 * (HOP3_SPIN + 144));
+                    mbar_arrive_expect_tx(b, 2 * (HOP3_SPIN + 144) + (clov ? 576 : 0));
                     tma_tile_2d(sl, &tm_in, 64 * RPT * h, 12 * jn, b);
                     tma_tile_2d(sl + HOP3_SPIN, &tm_in, 64 * RPT * h, 12 * jb, b);
                     bulk_g2s(sl + 2 * HOP3_SPIN, L + ((long)(p * 4 + mu) * Vh + cb) * 9, 144, b);
                     bulk_g2s(sl + 2 * HOP3_SPIN + 144, L + ((long)((1 - p) * 4 + mu) * Vh + jb) * 9, 144, b);
+                    if (clov) bulk_g2s(sl + 2 * HOP3_SPIN + 288, C + ((long)p * Vh + cb) * 144, 576, b);
                 } else {
                     mbar_arrive_expect_tx(b, HOP3_SPIN + 144);
                     tma_tile_2d(sl, &tm_in, 64 * RPT * h, 12 * jn, b);
@@ -387,7 +398,7 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, HOP3_MINB)
                                               reinterpret_cast<const E *>(sl_ + HOP3_SPIN) + 32 * q + lane, \
                                               32 * RPT, lk_ + 9, cb_);                                     \
             }                                                                                              \
-            release();                                                                                     \
+            if (!(CJ && MU == 3)) release();                                                               \
         }                                                                                                  \
     }
         if (HPJ == 2) {
@@ -407,12 +418,14 @@ __global__ void __launch_bounds__(HOP3_WARPS * 32, HOP3_MINB)
         }
 #undef HOP3_DIR
 #undef HOP3_PAIR
-        if (!ok || !wait()) {
+        if (CJ) {
+            if (!ok) break;   // the clover came with the last hop job, whose slot is still held
+        } else if (!ok || !wait()) {
             ok = false;
             break;
         }
         const unsigned char *sl = ring + cslot * HOP3_SLOT;
-        const float *cl = reinterpret_cast<const float *>(sl + HOP3_SPIN);
+        const float *cl = reinterpret_cast<const float *>(sl + (CJ ? 2 * HOP3_SPIN + 288 : HOP3_SPIN));
         float2 res[RPT][12];
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
@@ -509,7 +522,7 @@ static long launch_hop3(const DiracOp &op, int p, float hws, float hwt, E *out, 
                         const uint32_t *rcode = nullptr) {
     // one RHS per lane: two hops per job (the slot still leaves room for four blocks per SM)
     constexpr int HPJ = RPT == 1 ? 2 : 1;
-    constexpr size_t smem = (size_t)HOP3_WARPS * NS * (Hop3Geo<RPT, E, HPJ>::SLOT + 8 + 8);
+    constexpr size_t smem = (size_t)HOP3_WARPS * NS * (Hop3Geo<RPT, E, HPJ, hop3_cj<MODE, HPJ>()>::SLOT + 8 + 8);
     static int bpsm[64] = {0};
     static int nsm[64] = {0};
     int dev = 0;
