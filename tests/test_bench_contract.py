@@ -60,3 +60,16 @@ def test_cuda_arm_fails_loudly_without_gpu():
                   {"RANK": "0", "WORLD_SIZE": "1"})
     assert r.returncode != 0
     assert json_lines(r.stdout) == []
+
+
+def test_stencil_traffic_comes_from_the_current_kernel_profile():
+    """The bench's roofline.traffic is the committed ncu summary's DRAM bytes over algorithmic
+    bytes for the current stencil version; the profile must exist, name that version, and give a
+    ratio at least 1 (DRAM cannot move less than the kernel's compulsory bytes) for the default
+    workload and for its N_v = 112 variant (the stencil does not depend on N_v)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for wl in ("paper_24x128", "paper_24x128_nv112"):
+        r = bench.measured_traffic_ratio(wl, "dslash_fp32")
+        assert r is not None and 1.0 <= r < 3.0, (wl, r)
+    assert bench.measured_traffic_ratio("medium_16x32", "dslash_fp32") is None   # taken on another version
