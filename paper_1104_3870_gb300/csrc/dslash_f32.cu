@@ -207,15 +207,17 @@ __global__ void __launch_bounds__(128, MODE == HOP_APPLY ? 6 : 8) hop2_kernel(co
 
 // ------------------------------------------------------------------ TMA-fed hop
 // The same arithmetic as hop2_kernel, with the operands of every hop brought into shared
-// memory by the copy engine ahead of use.  A work unit is one warp: 32 right-hand sides of
-// one output site (nr = 32 * 2^k).  It consumes nine jobs in order — the eight hops
-// (forward mu = 0, backward mu = 0, forward mu = 1, ...) and an epilogue — each filling one
-// slot of the warp's private ring of NS slots:
-//   hop job       [12][32] float2 tile of the neighbour spinor (one 2D tensor copy) + 9 float4 link
-//   epilogue job  [12][32] float2 tile of z (modes with z) + the 144-float clover block of the site
-// While the warp computes job n, jobs n+1 .. n+NS-1 are in flight; the slot of job n is
-// refilled with job n+NS as soon as every lane has read it.  Lane 0 issues all copies, so a
-// job costs the warp a handful of instructions, and warps never wait on one another.
+// memory by the copy engine ahead of use.  A work unit is one warp: 32 RPT right-hand sides of
+// one output site.  It consumes its jobs in order, each filling one slot of the warp's private
+// ring of NS slots:
+//   hop job       [12][32 RPT] tile of a neighbour spinor (one 2D tensor copy) + its link (9
+//                 float4); with one RHS per lane a job holds both hops of one direction
+//   epilogue job  [12][32 RPT] tile of z (modes with z) + the 144-float clover block of the site
+// (nine jobs per site with two RHS per lane, five with one; in the clover-inverse mode with one
+// RHS per lane the clover rides in the last hop job, whose slot is kept through the epilogue:
+// four jobs).  While the warp computes job n, jobs n+1 .. n+NS-1 are in flight; the slot of job n
+// is refilled with job n+NS as soon as every lane has read it.  Lane 0 issues all copies, and
+// warps never wait on one another.
 constexpr int HOP3_WARPS = 4;
 #ifndef HOP3_MINB
 #define HOP3_MINB 4   // blocks per SM the register allocation targets
